@@ -1,0 +1,214 @@
+/*
+ * qsw.h -- C ABI of the GB300 L-QSW time-series library (libqsw.so).
+ *
+ * The library computes the time series of a locally-interacting quantum
+ * stochastic walk (L-QSW) on a weighted digraph,
+ *
+ *     rho~(t_k) = exp(t_k L~) rho~(0),   t_k = t0 + k dt,  k = 0..steps,
+ *
+ * where L~ is the N~^2 x N~^2 vectorised superoperator of the master equation
+ * (paper: QSW_MPI, arXiv:2003.02450, Section 2.4, Eqs. qsw, qsw_ss,
+ * vec_mappings, qsw_vec_sol), computed by Al-Mohy & Higham's truncated-Taylor
+ * scaling-and-squaring algorithms (paper Section 3.1: Algorithm 3.2 `step`,
+ * Algorithm 5.2 `series`, parameters from the 1-norm series of L~ that is
+ * precomputed at construction, Section 4 footnote).
+ *
+ * Conventions used by every call
+ * ------------------------------
+ * - Graphs: CSR with row = destination vertex i, column = source vertex j, so
+ *   that G[i][j] = w(v_i, v_j) is the weight of the arc j -> i
+ *   (Eq. adjacency_graph; the printed omega = 1 example of Section 4 fixes this
+ *   orientation).  Columns strictly increasing within a row, no self-loops
+ *   (simple graphs, Tr G = 0), weights finite and > 0.  Graph arrays are HOST
+ *   pointers; the library copies them.
+ * - Vectorisation is column-major: rho~[i + N~ j] = rho[i][j] (Section 2.4.3).
+ *   Sources, then sinks, are appended after the N graph vertices, in argument
+ *   order, so N~ = N + n_sources + n_sinks (Section 2.4.1).
+ * - Complex numbers are interleaved (re, im) pairs of doubles: a state vector
+ *   of n = N~^2 entries occupies 2n doubles (16 n bytes).
+ * - "d_" arguments are DEVICE pointers on the context's device, owned by the
+ *   caller; "h_" arguments are host pointers.  Every call is ordered on the
+ *   context's CUDA stream; calls that return results or statistics to the host
+ *   synchronise that stream before returning.
+ * - No exception crosses this boundary: every call returns a qsw_status and,
+ *   on failure, a message retrievable with qsw_last_error().  Failed calls
+ *   leave caller buffers in an unspecified state and leak nothing.
+ * - Index limits: N~^2 and nnz(L~) must each be < 2^31 (32-bit CSR indices,
+ *   as in the paper's Section 3.2); larger problems return QSW_ERR_TOO_LARGE.
+ */
+#ifndef QSW_H
+#define QSW_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QSW_OK = 0,
+  QSW_ERR_INVALID_ARG = 1,    /* bad pointer, size, CSR structure, time grid */
+  QSW_ERR_NOT_SIMPLE = 2,     /* self-loop or non-positive weight (Section 2.1: simple graphs) */
+  QSW_ERR_OMEGA_RANGE = 3,    /* omega outside [0, 1] (Eq. qsw) */
+  QSW_ERR_OOM = 4,            /* device allocation failed */
+  QSW_ERR_NOT_CONVERGED = 5,  /* a device loop hit its iteration or wait limit */
+  QSW_ERR_CUDA = 6,           /* any other CUDA runtime error */
+  QSW_ERR_TOO_LARGE = 7,      /* N~^2 or nnz(L~) does not fit 32-bit indices */
+  QSW_ERR_NOT_HERMITIAN = 8   /* caller-supplied H is not symmetric */
+} qsw_status;
+
+/* Arithmetic of the Taylor loop.
+ * QSW_C128: complex128 superoperator and vectors, tolerance 2^-53 (Section 5).
+ * QSW_C64_BULK: complex64 superoperator values and Taylor terms with FP32
+ *   accumulation of every matrix-vector product; the running Taylor sum, the
+ *   stop test's norms, the 1-norm estimates and the (m, s) choice stay FP64;
+ *   tolerance 2^-24 with its own theta table.  Not in the paper. */
+typedef enum { QSW_C128 = 0, QSW_C64_BULK = 1 } qsw_precision;
+
+typedef struct qsw_ctx qsw_ctx;   /* device + stream + workspace cache */
+typedef struct qsw_op qsw_op;     /* one assembled superoperator L~ */
+
+/* Weighted digraph / Hamiltonian in CSR (host arrays, see conventions). */
+typedef struct {
+  int32_t n;               /* vertices */
+  int32_t nnz;             /* stored entries */
+  const int32_t* rowptr;   /* [n + 1], rowptr[0] = 0, rowptr[n] = nnz */
+  const int32_t* col;      /* [nnz], strictly increasing within a row */
+  const double* w;         /* [nnz] */
+} qsw_csr;
+
+/* A source (feeding `vertex`) or a sink (draining `vertex`) with its rate
+ * Gamma or Theta (Section 2.4.1, Eq. qsw_ss).  The rate multiplies a unit
+ * jump operator and is not scaled by omega. */
+typedef struct {
+  int32_t vertex;
+  double rate;
+} qsw_port;
+
+/* Statistics of one qsw_expmv_series call (filled when non-null). */
+typedef struct {
+  int32_t m0, s0;            /* (m*, s) used for the first state, exp(t0 L~) rho0 */
+  int32_t m_star, s;         /* (m*, s) for the whole interval (steps * dt) L~ */
+  int32_t step_m, step_s;    /* (m*, s) of each dt step when steps <= s (else 0) */
+  int32_t outputs_per_block; /* d of Algorithm 5.2 (0 when steps <= s) */
+  int32_t jobs;              /* Taylor blocks executed */
+  int64_t matvecs;           /* applications of L~ performed */
+  double bytes_per_matvec;   /* algorithmic bytes of one application of L~ */
+  double kernel_ms;          /* device time of the series kernel */
+} qsw_series_stats;
+
+/* ---------------------------------------------------------------- context */
+
+/* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
+ * (a cudaStream_t; NULL selects the legacy default stream).  The stream is
+ * borrowed, not owned.  Errors: INVALID_ARG (null ctx / bad device), CUDA. */
+qsw_status qsw_create(qsw_ctx** ctx, int device, void* cuda_stream);
+
+/* Destroy a context and its workspace (ops must be destroyed first). */
+void qsw_destroy(qsw_ctx* ctx);
+
+/* Message of the last failed call on `ctx` ("" if none).  Owned by ctx. */
+const char* qsw_last_error(const qsw_ctx* ctx);
+
+/* ---------------------------------------------------------- construction */
+
+/* Build L~ for an L-QSW (paper Section 2.4, Eq. qsw_ss; condensed
+ * construction of Section 3.3, Eq. condensed_lindblads).
+ *   G        : the digraph (host CSR).  One jump operator sqrt(G_ij)|i><j| per
+ *              arc j -> i (Eq. lindblad), weighted by omega.
+ *   H        : the Hamiltonian (host CSR, real symmetric, N x N), used exactly
+ *              as given; NULL selects trans(1, G^u), the Laplacian of the
+ *              undirected companion G^u = max(G, G^T) (Eq. generator_matrix).
+ *   omega    : decoherence parameter in [0, 1] (Eq. qsw).
+ *   sources, n_sources, sinks, n_sinks : ports (may be NULL when the count is 0).
+ *   precision: a qsw_precision.
+ * On success *out receives a library-owned operator (free with
+ * qsw_op_destroy).  Construction also precomputes ||L~||_1 exactly and
+ * estimates ||L~^p||_1 for p = 2..9 (Section 4 footnote) on the device.
+ * Errors: INVALID_ARG, NOT_SIMPLE, OMEGA_RANGE, NOT_HERMITIAN, TOO_LARGE, OOM,
+ * CUDA.  Synchronises the stream. */
+qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H,
+                                   double omega, const qsw_port* sources, int32_t n_sources,
+                                   const qsw_port* sinks, int32_t n_sinks,
+                                   int32_t precision, qsw_op** out);
+
+/* Rebuild the values and the 1-norm series of `op` at a new omega, keeping
+ * its graph, Hamiltonian and ports (the package's set_omega, Section 4). */
+qsw_status qsw_set_omega(qsw_op* op, double omega);
+
+/* Sizes and norms of an operator.  norms[0] = ||L~||_1 (exact), norms[p-1] =
+ * estimate of ||L~^p||_1 for p = 2..9.  Any output pointer may be NULL. */
+qsw_status qsw_op_info(const qsw_op* op, int64_t* n_tilde, int64_t* n, int64_t* nnz,
+                       double* norms9);
+
+/* Copy the assembled CSR of L~ into caller device buffers: d_rowptr[n + 1],
+ * d_col[nnz], d_val[2 nnz] (complex128; for a QSW_C64_BULK operator its
+ * complex64 values are widened).  Any pointer may be NULL to skip that array.
+ * Used by tests and tools. */
+qsw_status qsw_op_export_csr(const qsw_op* op, int32_t* d_rowptr, int32_t* d_col,
+                             double* d_val);
+
+void qsw_op_destroy(qsw_op* op);
+
+/* ------------------------------------------------------------- evolution */
+
+/* d_state[n] (complex128) <- vec(rho0).  Exactly one of h_rho0 (N~ x N~
+ * complex128, column-major, interleaved) or h_populations (N~ doubles: a
+ * diagonal rho0, off-diagonals zero; Section 4 `initial_state`) is non-NULL.
+ * Errors: INVALID_ARG (both/neither given, trace not 1 within 1e-12). */
+qsw_status qsw_initial_state(const qsw_op* op, const double* h_rho0,
+                             const double* h_populations, double* d_state);
+
+/* One application y = L~ x (complex128 in and out; a QSW_C64_BULK operator
+ * computes in complex64 with FP32 accumulation and widens).  d_x, d_y: n
+ * complex128, must not overlap. */
+qsw_status qsw_apply(const qsw_op* op, const double* d_x, double* d_y);
+
+/* The L-QSW time series (Algorithm 5.2 `series`; steps = 0 gives Algorithm 3.2
+ * `step` at t0):
+ *   d_rho0 : n complex128 (device), vec(rho(0)).
+ *   t0, dt : start time and spacing, finite and >= 0.
+ *   steps  : q >= 0 intervals; the series has steps + 1 states, state k at
+ *            t0 + k dt (state 0 at t0).
+ *   d_out  : (steps+1) x n complex128 (device, state k at offset 2 n k
+ *            doubles) or NULL.
+ *   d_pops : (steps+1) x N~ doubles (device), p_i(t_k) = Re rho_ii(t_k), or NULL.
+ *   stats  : host struct or NULL.
+ * At least one of d_out / d_pops must be non-NULL.  Synchronises the stream.
+ * Errors: INVALID_ARG, OOM, NOT_CONVERGED (a device wait exceeded its limit),
+ * CUDA. */
+qsw_status qsw_expmv_series(qsw_op* op, const double* d_rho0, double t0, double dt,
+                            int32_t steps, double* d_out, double* d_pops,
+                            qsw_series_stats* stats);
+
+/* Same computation with HOST buffers: h_rho0 (n complex128), h_out / h_pops
+ * as d_out / d_pops above but in host memory (pinned memory is fastest).  The
+ * host<->device copies are part of the call. */
+qsw_status qsw_expmv_series_host(qsw_op* op, const double* h_rho0, double t0, double dt,
+                                 int32_t steps, double* h_out, double* h_pops,
+                                 qsw_series_stats* stats);
+
+/* Populations of `count` consecutive states: d_pops[c N~ + i] =
+ * Re d_rho_series[c n + i (N~ + 1)] (Section 2.3; `gather_populations`). */
+qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t count,
+                           double* d_pops);
+
+/* ----------------------------------------------------- host-side helpers */
+
+/* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
+ * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor
+ * coefficients of log(exp(-x) T_m(x)) (Al-Mohy & Higham, Section 3).  Pure
+ * host computation; no GPU needed. */
+qsw_status qsw_theta_table(int32_t precision, double* theta55);
+
+/* Code Fragment 3.1 of Al-Mohy & Higham for the matrix t L~, from norms9 as
+ * returned by qsw_op_info, n0 right-hand sides: *m_star, *s.  The same code
+ * runs on the device inside qsw_expmv_series.  Pure host computation. */
+qsw_status qsw_select_params(const double* norms9, double t, int32_t n0, int32_t precision,
+                             int32_t* m_star, int32_t* s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QSW_H */

@@ -1,0 +1,377 @@
+// The extern "C" boundary of libqsw.so (declared in include/qsw.h): argument
+// validation, object lifetime and error translation.  All arithmetic of the
+// path runs in the kernels of graph.cu, assemble.cu, norms.cu and series.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <exception>
+#include <memory>
+#include <new>
+
+#include "op.h"
+#include "params.cuh"
+
+using qsw::Error;
+using qsw::Op;
+
+namespace {
+
+thread_local std::string g_orphan_error;
+
+template <class F>
+qsw_status guarded(qsw_ctx* ctx, F&& f) {
+  try {
+    f();
+    if (ctx) ctx->last_error.clear();
+    return QSW_OK;
+  } catch (const Error& e) {
+    if (ctx) ctx->last_error = e.msg;
+    else g_orphan_error = e.msg;
+    return e.status;
+  } catch (const std::bad_alloc&) {
+    if (ctx) ctx->last_error = "host allocation failed";
+    return QSW_ERR_OOM;
+  } catch (const std::exception& e) {
+    if (ctx) ctx->last_error = e.what();
+    return QSW_ERR_INVALID_ARG;
+  }
+}
+
+void set_device(const qsw_ctx* ctx) { QSW_CUDA_TRY(cudaSetDevice(ctx->device)); }
+
+// Structural checks of a host CSR (see qsw.h conventions).
+void check_csr(const qsw_csr* m, const char* name, bool allow_diag) {
+  const std::string nm(name);
+  QSW_CHECK_ARG(m != nullptr, QSW_ERR_INVALID_ARG, nm + " is NULL");
+  QSW_CHECK_ARG(m->n >= 1, QSW_ERR_INVALID_ARG, nm + ".n must be >= 1");
+  QSW_CHECK_ARG(m->nnz >= 0, QSW_ERR_INVALID_ARG, nm + ".nnz must be >= 0");
+  QSW_CHECK_ARG(m->rowptr != nullptr, QSW_ERR_INVALID_ARG, nm + ".rowptr is NULL");
+  QSW_CHECK_ARG(m->nnz == 0 || (m->col && m->w), QSW_ERR_INVALID_ARG, nm + ".col/.w is NULL");
+  QSW_CHECK_ARG(m->rowptr[0] == 0 && m->rowptr[m->n] == m->nnz, QSW_ERR_INVALID_ARG,
+                nm + ".rowptr must start at 0 and end at nnz");
+  for (int i = 0; i < m->n; ++i) {
+    QSW_CHECK_ARG(m->rowptr[i] <= m->rowptr[i + 1], QSW_ERR_INVALID_ARG,
+                  nm + ".rowptr is not non-decreasing");
+    for (int e = m->rowptr[i]; e < m->rowptr[i + 1]; ++e) {
+      const int c = m->col[e];
+      QSW_CHECK_ARG(c >= 0 && c < m->n, QSW_ERR_INVALID_ARG, nm + ": column index out of range");
+      QSW_CHECK_ARG(e == m->rowptr[i] || m->col[e - 1] < c, QSW_ERR_INVALID_ARG,
+                    nm + ": columns must be strictly increasing within a row");
+      QSW_CHECK_ARG(isfinite(m->w[e]), QSW_ERR_INVALID_ARG, nm + ": non-finite value");
+      if (!allow_diag)
+        QSW_CHECK_ARG(c != i, QSW_ERR_NOT_SIMPLE, nm + ": self-loop (only simple graphs, Tr G = 0)");
+    }
+  }
+}
+
+double lookup(const qsw_csr* m, int i, int j, bool* found) {
+  const int* b = m->col + m->rowptr[i];
+  const int* e = m->col + m->rowptr[i + 1];
+  const int* p = std::lower_bound(b, e, j);
+  *found = p != e && *p == j;
+  return *found ? m->w[p - m->col] : 0.0;
+}
+
+void check_ports(const qsw_port* p, int count, int N, const char* name) {
+  QSW_CHECK_ARG(count >= 0 && count <= qsw::kMaxPorts, QSW_ERR_INVALID_ARG,
+                std::string(name) + ": bad count");
+  QSW_CHECK_ARG(count == 0 || p != nullptr, QSW_ERR_INVALID_ARG, std::string(name) + " is NULL");
+  for (int k = 0; k < count; ++k) {
+    QSW_CHECK_ARG(p[k].vertex >= 0 && p[k].vertex < N, QSW_ERR_INVALID_ARG,
+                  std::string(name) + ": vertex out of range");
+    QSW_CHECK_ARG(isfinite(p[k].rate) && p[k].rate > 0.0, QSW_ERR_INVALID_ARG,
+                  std::string(name) + ": rate must be finite and > 0");
+  }
+}
+
+void rebuild(Op& op) {
+  qsw::build_jumps(op);
+  qsw::Csr LH;
+  op.L = qsw::Csr{};
+  qsw::assemble(op, false, op.L);
+  qsw::assemble(op, true, LH);
+  qsw::compute_norms(op, op.L, LH);
+  LH = qsw::Csr{};
+  if (op.precision == QSW_C64_BULK) qsw::to_fp32(op, op.L);
+  op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
+}
+
+}  // namespace
+
+extern "C" {
+
+qsw_status qsw_create(qsw_ctx** out, int device, void* stream) {
+  return guarded(nullptr, [&] {
+    QSW_CHECK_ARG(out != nullptr, QSW_ERR_INVALID_ARG, "ctx is NULL");
+    *out = nullptr;
+    int count = 0;
+    QSW_CUDA_TRY(cudaGetDeviceCount(&count));
+    QSW_CHECK_ARG(device >= 0 && device < count, QSW_ERR_INVALID_ARG, "no such CUDA device");
+    QSW_CUDA_TRY(cudaSetDevice(device));
+    qsw_ctx* c = new qsw_ctx();
+    c->device = device;
+    c->stream = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+      delete c;
+      QSW_CUDA_TRY(e);
+    }
+    try {
+      qsw::upload_theta(device);
+    } catch (...) {
+      delete c;
+      throw;
+    }
+    *out = c;
+  });
+}
+
+void qsw_destroy(qsw_ctx* ctx) { delete ctx; }
+
+const char* qsw_last_error(const qsw_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : g_orphan_error.c_str();
+}
+
+qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, double omega,
+                                   const qsw_port* sources, int32_t n_sources,
+                                   const qsw_port* sinks, int32_t n_sinks, int32_t precision,
+                                   qsw_op** out) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr && out != nullptr, QSW_ERR_INVALID_ARG, "ctx/out is NULL");
+    *out = nullptr;
+    check_csr(G, "G", false);
+    for (int e = 0; e < G->nnz; ++e)
+      QSW_CHECK_ARG(G->w[e] > 0.0, QSW_ERR_NOT_SIMPLE, "G: arc weights must be > 0");
+    QSW_CHECK_ARG(isfinite(omega) && omega >= 0.0 && omega <= 1.0, QSW_ERR_OMEGA_RANGE,
+                  "omega must lie in [0, 1]");
+    QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
+                  "unknown precision");
+    if (H) {
+      check_csr(H, "H", true);
+      QSW_CHECK_ARG(H->n == G->n, QSW_ERR_INVALID_ARG, "H must be N x N");
+      for (int i = 0; i < H->n; ++i)
+        for (int e = H->rowptr[i]; e < H->rowptr[i + 1]; ++e) {
+          bool f = false;
+          const double v = lookup(H, H->col[e], i, &f);
+          QSW_CHECK_ARG(f && v == H->w[e], QSW_ERR_NOT_HERMITIAN, "H must be symmetric");
+        }
+    }
+    check_ports(sources, n_sources, G->n, "sources");
+    check_ports(sinks, n_sinks, G->n, "sinks");
+    const long long Nt = (long long)G->n + n_sources + n_sinks;
+    QSW_CHECK_ARG(Nt * Nt < (1LL << 31) - 1, QSW_ERR_TOO_LARGE,
+                  "N~^2 does not fit 32-bit indices");
+    set_device(ctx);
+
+    std::unique_ptr<Op> op(new Op());
+    op->ctx = ctx;
+    op->precision = precision;
+    op->omega = omega;
+    op->N = G->n;
+    op->Nt = (int)Nt;
+    op->n = Nt * Nt;
+    op->g_rowptr.assign(G->rowptr, G->rowptr + G->n + 1);
+    op->g_col.assign(G->col, G->col + G->nnz);
+    op->g_w.assign(G->w, G->w + G->nnz);
+    if (H) {
+      op->h_given = true;
+      op->h_rowptr.assign(H->rowptr, H->rowptr + H->n + 1);
+      op->h_col.assign(H->col, H->col + H->nnz);
+      op->h_w.assign(H->w, H->w + H->nnz);
+    }
+    for (int k = 0; k < n_sources; ++k) {
+      op->src_v.push_back(sources[k].vertex);
+      op->src_r.push_back(sources[k].rate);
+    }
+    for (int k = 0; k < n_sinks; ++k) {
+      op->snk_v.push_back(sinks[k].vertex);
+      op->snk_r.push_back(sinks[k].rate);
+    }
+    qsw::build_graph(*op);
+    rebuild(*op);
+    *out = reinterpret_cast<qsw_op*>(op.release());
+  });
+}
+
+qsw_status qsw_set_omega(qsw_op* h, double omega) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
+    QSW_CHECK_ARG(isfinite(omega) && omega >= 0.0 && omega <= 1.0, QSW_ERR_OMEGA_RANGE,
+                  "omega must lie in [0, 1]");
+    set_device(op->ctx);
+    op->omega = omega;
+    rebuild(*op);
+  });
+}
+
+qsw_status qsw_op_info(const qsw_op* h, int64_t* n_tilde, int64_t* n, int64_t* nnz,
+                       double* norms9) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
+    if (n_tilde) *n_tilde = op->Nt;
+    if (n) *n = op->n;
+    if (nnz) *nnz = op->L.nnz;
+    if (norms9) memcpy(norms9, op->norms, sizeof(double) * qsw::kNormPowers);
+  });
+}
+
+qsw_status qsw_op_export_csr(const qsw_op* h, int32_t* d_rowptr, int32_t* d_col, double* d_val) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
+    set_device(op->ctx);
+    cudaStream_t st = op->ctx->stream;
+    if (d_rowptr)
+      QSW_CUDA_TRY(cudaMemcpyAsync(d_rowptr, op->L.rowptr.p, sizeof(int) * (op->n + 1),
+                                   cudaMemcpyDeviceToDevice, st));
+    if (d_col)
+      QSW_CUDA_TRY(cudaMemcpyAsync(d_col, op->L.col.p, sizeof(int) * op->L.nnz,
+                                   cudaMemcpyDeviceToDevice, st));
+    if (d_val) {
+      if (!op->L.fp32) {
+        QSW_CUDA_TRY(cudaMemcpyAsync(d_val, op->L.val.p, sizeof(double2) * op->L.nnz,
+                                     cudaMemcpyDeviceToDevice, st));
+      } else {
+        qsw::widen_values(*op, d_val);
+      }
+    }
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+void qsw_op_destroy(qsw_op* h) {
+  Op* op = reinterpret_cast<Op*>(h);
+  if (!op) return;
+  cudaSetDevice(op->ctx->device);
+  cudaStreamSynchronize(op->ctx->stream);
+  delete op;
+}
+
+qsw_status qsw_initial_state(const qsw_op* h, const double* h_rho0, const double* h_pops,
+                             double* d_state) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr && d_state != nullptr, QSW_ERR_INVALID_ARG, "op/d_state is NULL");
+    QSW_CHECK_ARG((h_rho0 != nullptr) != (h_pops != nullptr), QSW_ERR_INVALID_ARG,
+                  "give exactly one of rho0 and populations");
+    set_device(op->ctx);
+    cudaStream_t st = op->ctx->stream;
+    const int Nt = op->Nt;
+    double tr = 0.0;
+    if (h_pops) {
+      for (int i = 0; i < Nt; ++i) {
+        QSW_CHECK_ARG(isfinite(h_pops[i]) && h_pops[i] >= 0.0, QSW_ERR_INVALID_ARG,
+                      "populations must be finite and >= 0");
+        tr += h_pops[i];
+      }
+      QSW_CHECK_ARG(fabs(tr - 1.0) <= 1e-12, QSW_ERR_INVALID_ARG, "populations must sum to 1");
+      qsw::DevBuf tmp;
+      tmp.alloc(sizeof(double) * Nt);
+      QSW_CUDA_TRY(cudaMemcpyAsync(tmp.p, h_pops, sizeof(double) * Nt, cudaMemcpyHostToDevice, st));
+      qsw::initial_state_from_pops(*op, tmp.as<double>(), d_state);
+      QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      for (int i = 0; i < Nt; ++i) tr += h_rho0[2 * ((size_t)i * Nt + i)];
+      QSW_CHECK_ARG(fabs(tr - 1.0) <= 1e-12, QSW_ERR_INVALID_ARG, "Tr rho0 must be 1");
+      QSW_CUDA_TRY(cudaMemcpyAsync(d_state, h_rho0, sizeof(double2) * op->n, cudaMemcpyHostToDevice,
+                                   st));
+      QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+  });
+}
+
+qsw_status qsw_apply(const qsw_op* h, const double* d_x, double* d_y) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr && d_x && d_y && d_x != d_y, QSW_ERR_INVALID_ARG,
+                  "bad arguments to qsw_apply");
+    set_device(op->ctx);
+    qsw::apply(*op, d_x, d_y);
+  });
+}
+
+static void check_series_args(const Op* op, const void* rho0, double t0, double dt, int steps,
+                              const void* out, const void* pops) {
+  QSW_CHECK_ARG(op != nullptr && rho0 != nullptr, QSW_ERR_INVALID_ARG, "op/rho0 is NULL");
+  QSW_CHECK_ARG(out != nullptr || pops != nullptr, QSW_ERR_INVALID_ARG,
+                "give an output array and/or a populations array");
+  QSW_CHECK_ARG(steps >= 0, QSW_ERR_INVALID_ARG, "steps must be >= 0");
+  QSW_CHECK_ARG(isfinite(t0) && t0 >= 0.0 && isfinite(dt) && dt >= 0.0, QSW_ERR_INVALID_ARG,
+                "t0 and dt must be finite and >= 0");
+  QSW_CHECK_ARG(isfinite(t0 + steps * dt), QSW_ERR_INVALID_ARG, "time grid overflows");
+}
+
+qsw_status qsw_expmv_series(qsw_op* h, const double* d_rho0, double t0, double dt, int32_t steps,
+                            double* d_out, double* d_pops, qsw_series_stats* stats) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    check_series_args(op, d_rho0, t0, dt, steps, d_out, d_pops);
+    set_device(op->ctx);
+    qsw::run_series(*op, d_rho0, t0, dt, steps, d_out, d_pops, stats);
+  });
+}
+
+qsw_status qsw_expmv_series_host(qsw_op* h, const double* h_rho0, double t0, double dt,
+                                 int32_t steps, double* h_out, double* h_pops,
+                                 qsw_series_stats* stats) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    check_series_args(op, h_rho0, t0, dt, steps, h_out, h_pops);
+    set_device(op->ctx);
+    cudaStream_t st = op->ctx->stream;
+    qsw::DevBuf rho0, out, pops;
+    rho0.alloc(sizeof(double2) * op->n);
+    if (h_out) out.alloc(sizeof(double2) * op->n * ((size_t)steps + 1));
+    if (h_pops) pops.alloc(sizeof(double) * op->Nt * ((size_t)steps + 1));
+    QSW_CUDA_TRY(cudaMemcpyAsync(rho0.p, h_rho0, sizeof(double2) * op->n, cudaMemcpyHostToDevice, st));
+    qsw::run_series(*op, rho0.as<double>(), t0, dt, steps, h_out ? out.as<double>() : nullptr,
+                    h_pops ? pops.as<double>() : nullptr, stats);
+    if (h_out)
+      QSW_CUDA_TRY(cudaMemcpyAsync(h_out, out.p, out.bytes, cudaMemcpyDeviceToHost, st));
+    if (h_pops)
+      QSW_CUDA_TRY(cudaMemcpyAsync(h_pops, pops.p, sizeof(double) * op->Nt * ((size_t)steps + 1),
+                                   cudaMemcpyDeviceToHost, st));
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  });
+}
+
+qsw_status qsw_populations(const qsw_op* h, const double* d_rho, int32_t count, double* d_pops) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr && d_rho && d_pops && count >= 0, QSW_ERR_INVALID_ARG,
+                  "bad arguments to qsw_populations");
+    if (count == 0) return;
+    set_device(op->ctx);
+    qsw::populations(*op, d_rho, count, d_pops);
+  });
+}
+
+qsw_status qsw_theta_table(int32_t precision, double* theta55) {
+  return guarded(nullptr, [&] {
+    QSW_CHECK_ARG(theta55 != nullptr, QSW_ERR_INVALID_ARG, "theta55 is NULL");
+    QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
+                  "unknown precision");
+    memcpy(theta55, qsw::theta_table(precision), sizeof(double) * qsw::kMMax);
+  });
+}
+
+qsw_status qsw_select_params(const double* norms9, double t, int32_t n0, int32_t precision,
+                             int32_t* m_star, int32_t* s) {
+  return guarded(nullptr, [&] {
+    QSW_CHECK_ARG(norms9 && m_star && s, QSW_ERR_INVALID_ARG, "NULL argument");
+    QSW_CHECK_ARG(n0 >= 1 && isfinite(t) && t >= 0.0, QSW_ERR_INVALID_ARG, "bad t or n0");
+    QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
+                  "unknown precision");
+    double dp[qsw::kNormPowers + 1] = {0};
+    dp[0] = norms9[0];
+    for (int p = 2; p <= qsw::kNormPowers; ++p) dp[p - 1] = pow(norms9[p - 1], 1.0 / p);
+    const qsw::Params r = qsw::select_params(dp, qsw::theta_table(precision), t, n0);
+    *m_star = r.m;
+    *s = r.s;
+  });
+}
+
+}  // extern "C"

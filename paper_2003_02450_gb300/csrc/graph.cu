@@ -1,0 +1,356 @@
+// Digraph normalisation on the device (paper Section 2.1-2.4).
+//
+//   G^T            : transpose of the adjacency (rows = source vertex).
+//   OutDeg(j)      : sum_i G_ij (Eq. out_degree) -- part of the jump rates.
+//   G^u            : max(G, G^T) (Section 2.1).
+//   H              : trans(1, G^u) = diag(OutDeg_{G^u}) - G^u (Eq. generator_matrix),
+//                    or the caller's symmetric H split into diagonal + off-diagonal.
+//   J, J^T         : the jump operators as weighted arc lists.  Row i of J
+//                    lists every jump |i><q| with its rate: omega * G_iq for the
+//                    graph's arcs (Eq. lindblad, weighted by omega in Eq. qsw),
+//                    Gamma for a source feeding i, Theta for the sink i
+//                    (Eq. qsw_ss, not omega-scaled).  J^T lists them by q.
+//   dtot(q)        : sum of the rates of the jumps leaving q, i.e. the diagonal
+//                    of sum_k tau_k L_k^dag L_k that enters the anticommutator.
+//
+// All lists come out sorted by column, and every floating-point sum is taken
+// in ascending index order, so the results are deterministic.
+#include "op.h"
+
+namespace qsw {
+namespace {
+
+__global__ void count_cols_kernel(int nnz, const int* __restrict__ col, int* __restrict__ cnt) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += gridDim.x * blockDim.x)
+    atomicAdd(&cnt[col[e]], 1);
+}
+
+// Exclusive scan of cnt[0..n) into out[0..n], out[n] = total.  One block.
+__global__ void scan_small_kernel(const int* __restrict__ cnt, int* __restrict__ out, int n) {
+  __shared__ long long part[1024];
+  const int t = threadIdx.x;
+  const int chunk = (n + blockDim.x - 1) / blockDim.x;
+  const int lo = t * chunk;
+  const int hi = min(n, lo + chunk);
+  long long s = 0;
+  for (int i = lo; i < hi; ++i) s += cnt[i];
+  part[t] = s;
+  __syncthreads();
+  if (t == 0) {
+    long long acc = 0;
+    for (int i = 0; i < (int)blockDim.x; ++i) {
+      const long long v = part[i];
+      part[i] = acc;
+      acc += v;
+    }
+    out[n] = (int)acc;
+  }
+  __syncthreads();
+  long long acc = part[t];
+  for (int i = lo; i < hi; ++i) {
+    out[i] = (int)acc;
+    acc += cnt[i];
+  }
+}
+
+__global__ void scatter_transpose_kernel(int N, const int* __restrict__ rowptr,
+                                         const int* __restrict__ col, const double* __restrict__ w,
+                                         int* __restrict__ cursor, int* __restrict__ tcol,
+                                         double* __restrict__ tw) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int pos = atomicAdd(&cursor[col[e]], 1);
+      tcol[pos] = i;
+      tw[pos] = w[e];
+    }
+  }
+}
+
+// Insertion sort of every row segment by column (segments are short).
+__global__ void sort_segments_kernel(int N, const int* __restrict__ rowptr, int* __restrict__ col,
+                                     double* __restrict__ val) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    const int lo = rowptr[i], hi = rowptr[i + 1];
+    for (int a = lo + 1; a < hi; ++a) {
+      const int c = col[a];
+      const double v = val[a];
+      int b = a - 1;
+      while (b >= lo && col[b] > c) {
+        col[b + 1] = col[b];
+        val[b + 1] = val[b];
+        --b;
+      }
+      col[b + 1] = c;
+      val[b + 1] = v;
+    }
+  }
+}
+
+// |row i of G  union  row i of G^T|
+__global__ void union_count_kernel(int N, const int* __restrict__ ar, const int* __restrict__ ac,
+                                   const int* __restrict__ br, const int* __restrict__ bc,
+                                   int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int a = ar[i], ae = ar[i + 1], b = br[i], be = br[i + 1], c = 0;
+    while (a < ae || b < be) {
+      const int ca = a < ae ? ac[a] : INT_MAX;
+      const int cb = b < be ? bc[b] : INT_MAX;
+      if (ca <= cb) ++a;
+      if (cb <= ca) ++b;
+      ++c;
+    }
+    cnt[i] = c;
+  }
+}
+
+// G^u row i = max over the union; H off-diagonal = -G^u, H_ii = sum_j G^u_ij.
+__global__ void laplacian_fill_kernel(int N, const int* __restrict__ ar, const int* __restrict__ ac,
+                                      const double* __restrict__ aw, const int* __restrict__ br,
+                                      const int* __restrict__ bc, const double* __restrict__ bw,
+                                      const int* __restrict__ urow, int* __restrict__ hcol,
+                                      double* __restrict__ hval, double* __restrict__ hdiag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int a = ar[i], ae = ar[i + 1], b = br[i], be = br[i + 1], pos = urow[i];
+    double deg = 0.0;
+    while (a < ae || b < be) {
+      const int ca = a < ae ? ac[a] : INT_MAX;
+      const int cb = b < be ? bc[b] : INT_MAX;
+      double wa = 0.0, wb = 0.0;
+      int c;
+      if (ca <= cb) { wa = aw[a]; c = ca; }
+      if (cb <= ca) { wb = bw[b]; c = cb; }
+      if (ca <= cb) ++a;
+      if (cb <= ca) ++b;
+      const double wu = wa > wb ? wa : wb;
+      hcol[pos] = c;
+      hval[pos] = -wu;
+      ++pos;
+      deg += wu;
+    }
+    hdiag[i] = deg;
+  }
+}
+
+__global__ void h_offcount_kernel(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                  int* __restrict__ cnt) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int c = 0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) c += col[e] != i;
+    cnt[i] = c;
+  }
+}
+
+__global__ void h_split_kernel(int N, const int* __restrict__ rowptr, const int* __restrict__ col,
+                               const double* __restrict__ w, const int* __restrict__ orow,
+                               int* __restrict__ ocol, double* __restrict__ oval,
+                               double* __restrict__ hdiag) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+    int pos = orow[i];
+    double dgl = 0.0;
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      if (col[e] == i) {
+        dgl = w[e];
+      } else {
+        ocol[pos] = col[e];
+        oval[pos] = w[e];
+        ++pos;
+      }
+    }
+    hdiag[i] = dgl;
+  }
+}
+
+struct PortArgs {
+  int N, Nt, n_src, n_snk;
+  const int* src_v;
+  const double* src_r;
+  const int* snk_v;
+  const double* snk_r;
+};
+
+// Row lengths of J (adjoint = 0, rows = destination) or J^T (rows = source).
+__global__ void jump_count_kernel(PortArgs pa, int graph_on, const int* __restrict__ grow,
+                                  int* __restrict__ cnt, int adjoint) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < pa.Nt; v += gridDim.x * blockDim.x) {
+    int c = 0;
+    if (v < pa.N) {
+      if (graph_on) c += grow[v + 1] - grow[v];
+      if (!adjoint) {
+        for (int s = 0; s < pa.n_src; ++s) c += pa.src_v[s] == v;
+      } else {
+        for (int z = 0; z < pa.n_snk; ++z) c += pa.snk_v[z] == v;
+      }
+    } else if (!adjoint && v >= pa.N + pa.n_src) {
+      c = 1;   // sink vertex: fed by the vertex it drains
+    } else if (adjoint && v < pa.N + pa.n_src) {
+      c = 1;   // source vertex: feeds its vertex
+    }
+    cnt[v] = c;
+  }
+}
+
+__global__ void jump_fill_kernel(PortArgs pa, int graph_on, double omega,
+                                 const int* __restrict__ grow, const int* __restrict__ gcol,
+                                 const double* __restrict__ gw, const int* __restrict__ jrow,
+                                 int* __restrict__ jcol, double* __restrict__ jval, int adjoint) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < pa.Nt; v += gridDim.x * blockDim.x) {
+    int pos = jrow[v];
+    if (v < pa.N) {
+      if (graph_on) {
+        for (int e = grow[v]; e < grow[v + 1]; ++e) {
+          jcol[pos] = gcol[e];
+          jval[pos] = omega * gw[e];
+          ++pos;
+        }
+      }
+      if (!adjoint) {
+        for (int s = 0; s < pa.n_src; ++s)
+          if (pa.src_v[s] == v) { jcol[pos] = pa.N + s; jval[pos] = pa.src_r[s]; ++pos; }
+      } else {
+        for (int z = 0; z < pa.n_snk; ++z)
+          if (pa.snk_v[z] == v) { jcol[pos] = pa.N + pa.n_src + z; jval[pos] = pa.snk_r[z]; ++pos; }
+      }
+    } else if (!adjoint && v >= pa.N + pa.n_src) {
+      const int z = v - pa.N - pa.n_src;
+      jcol[pos] = pa.snk_v[z];
+      jval[pos] = pa.snk_r[z];
+    } else if (adjoint && v < pa.N + pa.n_src) {
+      const int s = v - pa.N;
+      jcol[pos] = pa.src_v[s];
+      jval[pos] = pa.src_r[s];
+    }
+  }
+}
+
+__global__ void row_sum_kernel(int n, const int* __restrict__ rowptr, const double* __restrict__ val,
+                               double* __restrict__ out) {
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n; v += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) s += val[e];
+    out[v] = s;
+  }
+}
+
+template <class T>
+void upload(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
+  b.alloc(sizeof(T) * (h.size() ? h.size() : 1));
+  if (!h.empty())
+    QSW_CUDA_TRY(cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
+}
+
+int read_int(const int* d, cudaStream_t st) {
+  int v = 0;
+  QSW_CUDA_TRY(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  return v;
+}
+
+// cnt[0..n) -> rowptr[0..n]; returns the total.
+int scan_counts(DevBuf& cnt, DevBuf& rowptr, int n, cudaStream_t st) {
+  rowptr.alloc(sizeof(int) * (n + 1));
+  scan_small_kernel<<<1, 1024, 0, st>>>(cnt.as<int>(), rowptr.as<int>(), n);
+  QSW_CUDA_TRY(cudaGetLastError());
+  return read_int(rowptr.as<int>() + n, st);
+}
+
+}  // namespace
+
+void build_graph(Op& op) {
+  cudaStream_t st = op.ctx->stream;
+  GraphDev& g = op.g;
+  g.N = op.N;
+  g.Nt = op.Nt;
+  g.nnz_g = (int)op.g_col.size();
+  g.n_src = (int)op.src_v.size();
+  g.n_snk = (int)op.snk_v.size();
+  const int N = g.N;
+  upload(g.g_rowptr, op.g_rowptr, st);
+  upload(g.g_col, op.g_col, st);
+  upload(g.g_w, op.g_w, st);
+  upload(g.src_v, op.src_v, st);
+  upload(g.src_r, op.src_r, st);
+  upload(g.snk_v, op.snk_v, st);
+  upload(g.snk_r, op.snk_r, st);
+
+  // G^T: count per column, scan, scatter, sort segments.
+  g.scratch.alloc(sizeof(int) * (g.Nt + 1));
+  QSW_CUDA_TRY(cudaMemsetAsync(g.scratch.p, 0, sizeof(int) * (N + 1), st));
+  if (g.nnz_g)
+    count_cols_kernel<<<grid_for(g.nnz_g, 256, 4096), 256, 0, st>>>(g.nnz_g, g.g_col.as<int>(),
+                                                                     g.scratch.as<int>());
+  scan_counts(g.scratch, g.gt_rowptr, N, st);
+  g.gt_col.alloc(sizeof(int) * (g.nnz_g + 1));
+  g.gt_w.alloc(sizeof(double) * (g.nnz_g + 1));
+  QSW_CUDA_TRY(cudaMemcpyAsync(g.scratch.p, g.gt_rowptr.p, sizeof(int) * N,
+                               cudaMemcpyDeviceToDevice, st));
+  scatter_transpose_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+      N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.g_w.as<double>(), g.scratch.as<int>(),
+      g.gt_col.as<int>(), g.gt_w.as<double>());
+  sort_segments_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, g.gt_rowptr.as<int>(),
+                                                               g.gt_col.as<int>(), g.gt_w.as<double>());
+  QSW_CUDA_TRY(cudaGetLastError());
+
+  // Hamiltonian.
+  g.hdiag.alloc(sizeof(double) * g.Nt);
+  QSW_CUDA_TRY(cudaMemsetAsync(g.hdiag.p, 0, sizeof(double) * g.Nt, st));
+  if (!op.h_given) {
+    union_count_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+        N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.gt_rowptr.as<int>(), g.gt_col.as<int>(),
+        g.scratch.as<int>());
+    g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
+    g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
+    laplacian_fill_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+        N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.g_w.as<double>(), g.gt_rowptr.as<int>(),
+        g.gt_col.as<int>(), g.gt_w.as<double>(), g.hoff_rowptr.as<int>(), g.hoff_col.as<int>(),
+        g.hoff_val.as<double>(), g.hdiag.as<double>());
+  } else {
+    DevBuf hr, hc, hw;
+    upload(hr, op.h_rowptr, st);
+    upload(hc, op.h_col, st);
+    upload(hw, op.h_w, st);
+    h_offcount_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, hr.as<int>(), hc.as<int>(),
+                                                               g.scratch.as<int>());
+    g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
+    g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
+    h_split_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+        N, hr.as<int>(), hc.as<int>(), hw.as<double>(), g.hoff_rowptr.as<int>(),
+        g.hoff_col.as<int>(), g.hoff_val.as<double>(), g.hdiag.as<double>());
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));   // hr/hc/hw die at scope exit
+  }
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
+void build_jumps(Op& op) {
+  cudaStream_t st = op.ctx->stream;
+  GraphDev& g = op.g;
+  const int Nt = g.Nt;
+  const int graph_on = op.omega > 0.0;
+  PortArgs pa{g.N, Nt, g.n_src, g.n_snk, g.src_v.as<int>(), g.src_r.as<double>(),
+              g.snk_v.as<int>(), g.snk_r.as<double>()};
+  for (int adjoint = 0; adjoint < 2; ++adjoint) {
+    DevBuf& rp = adjoint ? g.jt_rowptr : g.j_rowptr;
+    DevBuf& cl = adjoint ? g.jt_col : g.j_col;
+    DevBuf& vl = adjoint ? g.jt_val : g.j_val;
+    const int* grow = adjoint ? g.gt_rowptr.as<int>() : g.g_rowptr.as<int>();
+    const int* gcol = adjoint ? g.gt_col.as<int>() : g.g_col.as<int>();
+    const double* gw = adjoint ? g.gt_w.as<double>() : g.g_w.as<double>();
+    jump_count_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, grow,
+                                                               g.scratch.as<int>(), adjoint);
+    QSW_CUDA_TRY(cudaGetLastError());
+    const int total = scan_counts(g.scratch, rp, Nt, st);
+    cl.alloc(sizeof(int) * (total + 1));
+    vl.alloc(sizeof(double) * (total + 1));
+    jump_fill_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, op.omega, grow, gcol,
+                                                              gw, rp.as<int>(), cl.as<int>(),
+                                                              vl.as<double>(), adjoint);
+    QSW_CUDA_TRY(cudaGetLastError());
+  }
+  g.dtot.alloc(sizeof(double) * Nt);
+  row_sum_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(Nt, g.jt_rowptr.as<int>(),
+                                                          g.jt_val.as<double>(), g.dtot.as<double>());
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
+}  // namespace qsw

@@ -1,0 +1,392 @@
+// The 1-norm series of L~ (paper Section 4 footnote: {||L~^p||_1, p = 1..9},
+// computed once per operator and reused for every t at the same omega).
+//
+//   ||L~||_1 exactly: the largest row sum of moduli of L~^H (= largest column
+//   sum of L~), a max-reduction, hence deterministic.
+//   ||L~^p||_1, p = 2..9: the block 1-norm estimator of Higham & Tisseur
+//   (2000, Algorithm 2.4), complex form (sign(z) = z/|z|, sign(0) = 1, products
+//   with (L~^H)^p, no parallel-column tests), t = 2 columns, itmax = 5.  The
+//   starting block is [1, x] / n with x_i = +-1 from the counter-based
+//   SplitMix64 generator (Steele, Lea & Flood 2014) at a fixed seed; ties in
+//   the row-norm ranking go to the smaller index.
+//
+// Every product and reduction runs in FP64 on the device; the host only
+// follows the algorithm's branches on the few scalars each iteration returns.
+// All reductions use a fixed grid and a fixed summation order, so repeated
+// builds give bit-identical estimates.
+#include <math.h>
+
+#include <algorithm>
+
+#include "op.h"
+
+namespace qsw {
+namespace {
+
+constexpr int kRedBlock = 256;
+constexpr int kRedGrid = 512;
+constexpr unsigned long long kSeed = 0x51535700ULL;
+constexpr int kItMax = 5;
+constexpr int kMaxExcl = 16;
+
+__device__ __forceinline__ double cabs(double2 z) { return hypot(z.x, z.y); }
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long i) {
+  unsigned long long z = seed + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// Y[n x t] = A X[n x t], row-major blocks, one 8-lane group per row.
+__global__ void spmm_kernel(int n, int t, const int* __restrict__ rowptr, const int* __restrict__ col,
+                            const double2* __restrict__ val, const double2* __restrict__ X,
+                            double2* __restrict__ Y) {
+  constexpr int G = 8;
+  const int lane = threadIdx.x % G;
+  const long long wg = (blockIdx.x * (long long)blockDim.x + threadIdx.x) / 32;
+  const long long stride = (long long)gridDim.x * blockDim.x / G;
+  // warp-uniform row loop: every lane takes part in the group shuffles
+  for (long long rb = wg * (32 / G); rb < n; rb += stride) {
+    const long long r = rb + (threadIdx.x % 32) / G;
+    const bool valid = r < n;
+    const int e0 = valid ? rowptr[r] : 0, e1 = valid ? rowptr[r + 1] : 0;
+    double2 acc0 = make_double2(0, 0), acc1 = make_double2(0, 0);
+    for (int e = e0 + lane; e < e1; e += G) {
+      const double2 v = val[e];
+      const long long c = col[e];
+      const double2 x0 = X[c * t];
+      acc0.x = fma(v.x, x0.x, fma(-v.y, x0.y, acc0.x));
+      acc0.y = fma(v.x, x0.y, fma(v.y, x0.x, acc0.y));
+      if (t > 1) {
+        const double2 x1 = X[c * t + 1];
+        acc1.x = fma(v.x, x1.x, fma(-v.y, x1.y, acc1.x));
+        acc1.y = fma(v.x, x1.y, fma(v.y, x1.x, acc1.y));
+      }
+    }
+    for (int o = G / 2; o > 0; o >>= 1) {
+      acc0.x += __shfl_xor_sync(0xffffffffu, acc0.x, o);
+      acc0.y += __shfl_xor_sync(0xffffffffu, acc0.y, o);
+      acc1.x += __shfl_xor_sync(0xffffffffu, acc1.x, o);
+      acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
+    }
+    if (valid && lane == 0) {
+      Y[r * t] = acc0;
+      if (t > 1) Y[r * t + 1] = acc1;
+    }
+  }
+}
+
+// Per-block sums of |Y(:, c)|, c < t; partials[b * 2 + c].
+__global__ void colabs_partial_kernel(int n, int t, const double2* __restrict__ Y,
+                                      double* __restrict__ partials) {
+  __shared__ double s0[kRedBlock], s1[kRedBlock];
+  double a0 = 0, a1 = 0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    a0 += cabs(Y[r * t]);
+    if (t > 1) a1 += cabs(Y[r * t + 1]);
+  }
+  s0[threadIdx.x] = a0;
+  s1[threadIdx.x] = a1;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      s0[threadIdx.x] += s0[threadIdx.x + o];
+      s1[threadIdx.x] += s1[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x * 2] = s0[0];
+    partials[blockIdx.x * 2 + 1] = s1[0];
+  }
+}
+
+__global__ void sum_partials_kernel(int nparts, const double* __restrict__ partials,
+                                    double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double a0 = 0, a1 = 0;
+    for (int b = 0; b < nparts; ++b) {
+      a0 += partials[b * 2];
+      a1 += partials[b * 2 + 1];
+    }
+    out[0] = a0;
+    out[1] = a1;
+  }
+}
+
+__global__ void sign_kernel(long long m, const double2* __restrict__ Y, double2* __restrict__ S) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 y = Y[e];
+    const double a = cabs(y);
+    S[e] = a == 0.0 ? make_double2(1.0, 0.0) : make_double2(y.x / a, y.y / a);
+  }
+}
+
+__global__ void rowmax_kernel(int n, int t, const double2* __restrict__ Z, double* __restrict__ h) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    double v = cabs(Z[r * t]);
+    if (t > 1) v = fmax(v, cabs(Z[r * t + 1]));
+    h[r] = v;
+  }
+}
+
+struct Excl {
+  int n;
+  int idx[kMaxExcl];
+};
+
+__device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
+  // larger value first, ties to the smaller index; ia < 0 means "none"
+  if (ib < 0) return ia >= 0;
+  if (ia < 0) return false;
+  return va > vb || (va == vb && ia < ib);
+}
+
+__global__ void argmax_partial_kernel(int n, const double* __restrict__ h, Excl ex,
+                                      double* __restrict__ pv, int* __restrict__ pi) {
+  __shared__ double sv[kRedBlock];
+  __shared__ int si[kRedBlock];
+  double bv = 0;
+  int bi = -1;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    bool skip = false;
+    for (int q = 0; q < ex.n; ++q) skip |= ex.idx[q] == (int)r;
+    if (skip) continue;
+    const double v = h[r];
+    if (better(v, (int)r, bv, bi)) { bv = v; bi = (int)r; }
+  }
+  sv[threadIdx.x] = bv;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) {
+      if (better(sv[threadIdx.x + o], si[threadIdx.x + o], sv[threadIdx.x], si[threadIdx.x])) {
+        sv[threadIdx.x] = sv[threadIdx.x + o];
+        si[threadIdx.x] = si[threadIdx.x + o];
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    pv[blockIdx.x] = sv[0];
+    pi[blockIdx.x] = si[0];
+  }
+}
+
+__global__ void argmax_final_kernel(int nparts, const double* __restrict__ pv,
+                                    const int* __restrict__ pi, const double* __restrict__ h,
+                                    int probe, double* __restrict__ out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double bv = 0;
+    int bi = -1;
+    for (int b = 0; b < nparts; ++b)
+      if (better(pv[b], pi[b], bv, bi)) { bv = pv[b]; bi = pi[b]; }
+    out[0] = bv;
+    out[1] = (double)bi;
+    out[2] = probe >= 0 ? h[probe] : 0.0;
+  }
+}
+
+__global__ void init_block_kernel(int n, int t, double2* __restrict__ X) {
+  const double inv = 1.0 / n;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    X[r * t] = make_double2(inv, 0.0);
+    if (t > 1) {
+      const bool neg = (splitmix64(kSeed, (unsigned long long)r) >> 63) != 0;
+      X[r * t + 1] = make_double2(neg ? -inv : inv, 0.0);
+    }
+  }
+}
+
+__global__ void set_units_kernel(int t, double2* __restrict__ X, int i0, int i1) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    X[(long long)i0 * t] = make_double2(1.0, 0.0);
+    if (t > 1) X[(long long)i1 * t + 1] = make_double2(1.0, 0.0);
+  }
+}
+
+// ||L||_1 = max over rows of L^H of sum |entry|
+__global__ void rowabs_max_kernel(int n, const int* __restrict__ rowptr,
+                                  const double2* __restrict__ val,
+                                  unsigned long long* __restrict__ out_bits) {
+  double best = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int e = rowptr[r]; e < rowptr[r + 1]; ++e) s += cabs(val[e]);
+    best = fmax(best, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(best));
+}
+
+__global__ void roots_kernel(const double* __restrict__ norms, double* __restrict__ dp) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    dp[0] = norms[0];
+    for (int p = 2; p <= kNormPowers; ++p) dp[p - 1] = pow(norms[p - 1], 1.0 / p);
+    dp[kNormPowers] = 0.0;
+  }
+}
+
+struct Estimator {
+  cudaStream_t st;
+  int n, t;
+  const Csr* A;
+  const Csr* AH;
+  DevBuf X, Y, W, h, partials, pv, pi, out;
+
+  void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
+
+  void mult(const Csr& M, int p, const double2* in, double2* out_, double2* tmp) {
+    // out = M^p in, ping-ponging through tmp
+    const double2* src = in;
+    for (int k = 0; k < p; ++k) {
+      double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
+      spmm_kernel<<<grid_for((long long)n * 8, 256, 152 * 16), 256, 0, st>>>(
+          n, t, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
+      src = dst;
+    }
+    QSW_CUDA_TRY(cudaGetLastError());
+  }
+
+  void colnorms(const double2* Yp, double* host2) {
+    colabs_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, t, Yp, partials.as<double>());
+    sum_partials_kernel<<<1, 32, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
+    QSW_CUDA_TRY(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+  }
+
+  // argmax of h over indices not in ex; also returns h[probe]
+  void argmax(const std::vector<int>& ex, int probe, double* best, int* idx, double* hprobe) {
+    Excl e{};
+    e.n = (int)std::min<size_t>(ex.size(), kMaxExcl);
+    for (int q = 0; q < e.n; ++q) e.idx[q] = ex[q];
+    argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, h.as<double>(), e, pv.as<double>(),
+                                                          pi.as<int>());
+    argmax_final_kernel<<<1, 32, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
+                                          probe, out.as<double>());
+    double o[3];
+    QSW_CUDA_TRY(cudaMemcpyAsync(o, out.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    sync();
+    *best = o[0];
+    *idx = (int)o[1];
+    if (hprobe) *hprobe = o[2];
+  }
+
+  double estimate(int p) {
+    double2* Xp = X.as<double2>();
+    double2* Yp = Y.as<double2>();
+    double2* Wp = W.as<double2>();
+    init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Xp);
+    QSW_CUDA_TRY(cudaGetLastError());
+    std::vector<int> hist;
+    double est_old = 0.0, est = 0.0;
+    int ind[2] = {0, 0};
+    int ind_best = 0;
+    for (int k = 1;; ++k) {
+      mult(*A, p, Xp, Yp, Wp);
+      double cn[2] = {0, 0};
+      colnorms(Yp, cn);
+      const int jbest = (t > 1 && cn[1] > cn[0]) ? 1 : 0;
+      est = cn[jbest];
+      if (est > est_old || k == 2) ind_best = ind[jbest];
+      if (k >= 2 && est <= est_old) {
+        est = est_old;
+        break;
+      }
+      est_old = est;
+      if (k > kItMax) break;
+      sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>((long long)n * t, Yp, Xp);
+      mult(*AH, p, Xp, Yp, Wp);   // Z = (A^H)^p S, in Y
+      rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
+      QSW_CUDA_TRY(cudaGetLastError());
+      double hmax, hbest;
+      int imax;
+      argmax({}, ind_best, &hmax, &imax, &hbest);
+      if (k >= 2 && hmax == hbest) break;
+      int fresh[2] = {-1, -1};
+      if (t > 1) {
+        double v2;
+        int i2;
+        argmax({imax}, -1, &v2, &i2, nullptr);
+        const bool in0 = std::find(hist.begin(), hist.end(), imax) != hist.end();
+        const bool in1 = std::find(hist.begin(), hist.end(), i2) != hist.end();
+        if (in0 && in1) break;
+        std::vector<int> ex = hist;
+        double fv;
+        argmax(ex, -1, &fv, &fresh[0], nullptr);
+        ex.push_back(fresh[0]);
+        argmax(ex, -1, &fv, &fresh[1], nullptr);
+        if (fresh[0] < 0 || fresh[1] < 0) break;   // fewer than t unused unit vectors
+      } else {
+        fresh[0] = imax;
+      }
+      ind[0] = fresh[0];
+      ind[1] = fresh[1];
+      QSW_CUDA_TRY(cudaMemsetAsync(Xp, 0, sizeof(double2) * (size_t)n * t, st));
+      set_units_kernel<<<1, 32, 0, st>>>(t, Xp, ind[0], ind[1] < 0 ? 0 : ind[1]);
+      QSW_CUDA_TRY(cudaGetLastError());
+      hist.push_back(ind[0]);
+      if (t > 1) hist.push_back(ind[1]);
+    }
+    return est;
+  }
+};
+
+}  // namespace
+
+void compute_norms(Op& op, const Csr& L, const Csr& LH) {
+  cudaStream_t st = op.ctx->stream;
+  const int n = (int)op.n;
+  // exact ||L||_1
+  DevBuf bits;
+  bits.alloc(sizeof(unsigned long long));
+  QSW_CUDA_TRY(cudaMemsetAsync(bits.p, 0, sizeof(unsigned long long), st));
+  rowabs_max_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, LH.rowptr.as<int>(),
+                                                                 LH.val.as<double2>(),
+                                                                 bits.as<unsigned long long>());
+  QSW_CUDA_TRY(cudaGetLastError());
+  unsigned long long b = 0;
+  QSW_CUDA_TRY(cudaMemcpyAsync(&b, bits.p, sizeof(b), cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  double one;
+  memcpy(&one, &b, sizeof(one));
+  op.norms[0] = one;
+
+  Estimator E;
+  E.st = st;
+  E.n = n;
+  E.t = n >= 2 ? kEll : 1;
+  E.A = &L;
+  E.AH = &LH;
+  E.X.alloc(sizeof(double2) * (size_t)n * E.t);
+  E.Y.alloc(sizeof(double2) * (size_t)n * E.t);
+  E.W.alloc(sizeof(double2) * (size_t)n * E.t);
+  E.h.alloc(sizeof(double) * n);
+  E.partials.alloc(sizeof(double) * 2 * kRedGrid);
+  E.pv.alloc(sizeof(double) * kRedGrid);
+  E.pi.alloc(sizeof(int) * kRedGrid);
+  E.out.alloc(sizeof(double) * 4);
+  for (int p = 2; p <= kNormPowers; ++p) op.norms[p - 1] = one == 0.0 ? 0.0 : E.estimate(p);
+
+  // d_p = ||L^p||_1^(1/p), taken on the device; the host keeps a copy for sizing.
+  DevBuf nd;
+  nd.alloc(sizeof(double) * kNormPowers);
+  QSW_CUDA_TRY(cudaMemcpyAsync(nd.p, op.norms, sizeof(double) * kNormPowers,
+                               cudaMemcpyHostToDevice, st));
+  op.dp_dev.alloc(sizeof(double) * (kNormPowers + 1));
+  roots_kernel<<<1, 32, 0, st>>>(nd.as<double>(), op.dp_dev.as<double>());
+  QSW_CUDA_TRY(cudaGetLastError());
+  QSW_CUDA_TRY(cudaMemcpyAsync(op.dp, op.dp_dev.p, sizeof(double) * (kNormPowers + 1),
+                               cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+}  // namespace qsw

@@ -1,0 +1,91 @@
+// Context and operator objects behind the opaque handles of qsw.h.
+#pragma once
+
+#include "qsw_internal.h"
+
+struct qsw_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int num_sms = 0;
+  std::string last_error;
+};
+
+namespace qsw {
+
+// Device-side graph data of one walk (Section 2.1-2.4 normalisation).
+struct GraphDev {
+  int N = 0;        // graph vertices
+  int Nt = 0;       // N~ = N + sources + sinks
+  int nnz_g = 0;
+  DevBuf g_rowptr, g_col, g_w;       // G (row = destination)
+  DevBuf gt_rowptr, gt_col, gt_w;    // G^T (row = source)
+  DevBuf hdiag;                      // [Nt] diagonal of H (0 beyond N)
+  DevBuf hoff_rowptr, hoff_col, hoff_val;  // off-diagonal H, N rows
+  int nnz_hoff = 0;
+  DevBuf src_v, src_r, snk_v, snk_r;       // ports
+  int n_src = 0, n_snk = 0;
+  // jump lists (coefficient included, omega-scaled for graph arcs)
+  DevBuf j_rowptr, j_col, j_val;     // rows = destination i (for L)
+  DevBuf jt_rowptr, jt_col, jt_val;  // rows = source q (for L^H)
+  DevBuf dtot;                       // [Nt] total jump rate leaving each vertex
+  DevBuf scratch;                    // small integer scratch
+};
+
+struct Csr {
+  DevBuf rowptr, col, val;   // val: double2 (c128) or float2 (c64)
+  int64_t nnz = 0;
+  bool fp32 = false;
+};
+
+struct Op {
+  qsw_ctx* ctx = nullptr;
+  int precision = QSW_C128;
+  double omega = 0.0;
+  int N = 0, Nt = 0;
+  int64_t n = 0;
+  // host copies kept for set_omega
+  std::vector<int> g_rowptr, g_col;
+  std::vector<double> g_w;
+  bool h_given = false;
+  std::vector<int> h_rowptr, h_col;
+  std::vector<double> h_w;
+  std::vector<int> src_v, snk_v;
+  std::vector<double> src_r, snk_r;
+
+  GraphDev g;
+  Csr L;           // the superoperator
+  double norms[kNormPowers] = {0};   // ||L||_1, est ||L^p||_1
+  double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
+  DevBuf dp_dev;
+  int tpr = 8;     // SpMV threads per row
+
+  // series workspace
+  DevBuf kbuf, ring, jobs, ctrl;
+};
+
+// graph.cu
+void build_graph(Op& op);           // uploads host graph, builds G^T, G^u, H, ports
+void build_jumps(Op& op);           // J, J^T, dtot for op.omega
+// assemble.cu
+void assemble(Op& op, bool adjoint, Csr& out);   // L (adjoint = false) or L^H, FP64 values
+void to_fp32(Op& op, Csr& m);                    // replace FP64 values by FP32
+// norms.cu
+void compute_norms(Op& op, const Csr& L, const Csr& LH);
+// series.cu
+void upload_theta(int device);
+void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
+                double* d_pops, qsw_series_stats* stats);
+void apply(const Op& op, const double* d_x, double* d_y);
+void populations(const Op& op, const double* d_rho, int count, double* d_pops);
+void initial_state_from_pops(const Op& op, const double* d_pops, double* d_state);
+void widen_values(const Op& op, double* d_val);
+int choose_tpr(double avg_row);
+
+inline unsigned grid_for(int64_t items, int block, int max_blocks = 1 << 20) {
+  int64_t b = (items + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (unsigned)b;
+}
+
+}  // namespace qsw

@@ -1,0 +1,112 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qsw.h"
+
+namespace qsw {
+
+constexpr int kMMax = 55;     // m_max of Al-Mohy & Higham Code Fragment 3.1
+constexpr int kPMax = 8;      // p_max (largest p with p(p-1) <= m_max + 1)
+constexpr int kEll = 2;       // columns of the 1-norm estimator
+constexpr int kNormPowers = 9;  // ||L^p||_1, p = 1..9 (paper Section 4 footnote)
+constexpr int kMaxPorts = 4096;
+
+// ------------------------------------------------------------------ errors
+struct Error {
+  qsw_status status;
+  std::string msg;
+};
+
+#define QSW_CUDA_TRY(expr)                                                         \
+  do {                                                                             \
+    cudaError_t e_ = (expr);                                                       \
+    if (e_ != cudaSuccess) {                                                       \
+      throw ::qsw::Error{e_ == cudaErrorMemoryAllocation ? QSW_ERR_OOM : QSW_ERR_CUDA, \
+                         std::string(#expr) + ": " + cudaGetErrorString(e_)};      \
+    }                                                                              \
+  } while (0)
+
+#define QSW_CHECK_ARG(cond, code, text)              \
+  do {                                                \
+    if (!(cond)) throw ::qsw::Error{(code), (text)};  \
+  } while (0)
+
+// ------------------------------------------------------------ device memory
+// RAII device buffer (cudaMalloc/cudaFree on the context's device).
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf& operator=(DevBuf&& o) noexcept {
+    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    return *this;
+  }
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  void alloc(size_t nbytes) {
+    if (nbytes <= bytes && p) return;
+    release();
+    if (nbytes == 0) return;
+    QSW_CUDA_TRY(cudaMalloc(&p, nbytes));
+    bytes = nbytes;
+  }
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ----------------------------------------------------- parameter selection
+// theta tables (host copy; the device copy lives in __constant__ memory of
+// series.cu).  theta[prec][m-1], m = 1..55.
+const double* theta_table(int precision);   // computes on first use
+double tolerance(int precision);
+
+// Outcome of Code Fragment 3.1 for one matrix t*L.
+struct Params {
+  int m;
+  int s;
+};
+
+// dp[0] = ||L||_1 (exact), dp[p-1] = ||L^p||_1^(1/p) for p = 2..9.
+// Identical code on host and device (IEEE operations only: *, /, ceil, <=).
+__host__ __device__ Params select_params(const double* dp, const double* theta, double t, int n0);
+
+// One Taylor block of the device program: outputs F_k = sum_p (k/d)^p Khat_p,
+// k = 1..d, with Khat_p = (hspan/p) L Khat_{p-1}, Khat_0 = Z.
+struct Job {
+  int z_slot;        // slot of Z (-1: the caller's rho0)
+  int out_slot0;     // slot of F_1; F_k in slot out_slot0 + k - 1 (mod ring)
+  int out_index0;    // series index of F_1 (for populations), or -1
+  int d;             // outputs in this block
+  int m;             // m* (max Taylor degree)
+  int final_outputs; // 1 if F_k are final series states (write populations)
+  double hspan;      // d * h: Khat_p = (hspan/p) L Khat_{p-1}
+};
+
+// Whole-series plan (Algorithm 5.2, with Algorithm 3.2 for the first state
+// and for the stepwise branch).  Built identically on host and device.
+struct PlanInfo {
+  int njobs;
+  int max_d;
+  int m0, s0, m_star, s, step_m, step_s, d;
+};
+
+// Writes up to max_jobs jobs (jobs may be null to only count).  `ring` > 0
+// maps series index k to slot k % ring (workspace ring); ring == 0 maps index
+// k to slot k (caller's output array).
+__host__ __device__ PlanInfo plan_series(const double* dp, const double* theta, double t0,
+                                         double dt, int steps, int n0, int ring, Job* jobs,
+                                         int max_jobs);
+
+}  // namespace qsw

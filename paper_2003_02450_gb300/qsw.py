@@ -1,0 +1,247 @@
+"""ctypes binding of libqsw.so (include/qsw.h), one Python function per C entry
+point with the same name.  Argument marshalling only: every step of the
+computation runs in the library's CUDA kernels.  Device buffers are passed as
+integer device pointers (e.g. ``torch.Tensor.data_ptr()``).
+
+If the library has not been built the first call raises ``QswUnavailable``;
+there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_void_p
+
+import numpy as np
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsw.so")
+
+QSW_C128 = 0
+QSW_C64_BULK = 1
+PRECISIONS = {"c128": QSW_C128, "c64": QSW_C64_BULK}
+
+STATUS = {0: "QSW_OK", 1: "QSW_ERR_INVALID_ARG", 2: "QSW_ERR_NOT_SIMPLE",
+          3: "QSW_ERR_OMEGA_RANGE", 4: "QSW_ERR_OOM", 5: "QSW_ERR_NOT_CONVERGED",
+          6: "QSW_ERR_CUDA", 7: "QSW_ERR_TOO_LARGE", 8: "QSW_ERR_NOT_HERMITIAN"}
+
+
+class QswUnavailable(RuntimeError):
+    """libqsw.so is missing or cannot be loaded."""
+
+
+class QswError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+        self.name = STATUS.get(status, str(status))
+        self.message = message
+
+
+class qsw_csr(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("nnz", c_int32), ("rowptr", POINTER(c_int32)),
+                ("col", POINTER(c_int32)), ("w", POINTER(c_double))]
+
+
+class qsw_port(ctypes.Structure):
+    _fields_ = [("vertex", c_int32), ("rate", c_double)]
+
+
+class qsw_series_stats(ctypes.Structure):
+    _fields_ = [("m0", c_int32), ("s0", c_int32), ("m_star", c_int32), ("s", c_int32),
+                ("step_m", c_int32), ("step_s", c_int32), ("outputs_per_block", c_int32),
+                ("jobs", c_int32), ("matvecs", c_int64), ("bytes_per_matvec", c_double),
+                ("kernel_ms", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+_SIGNATURES = {
+    "qsw_create": ([POINTER(c_void_p), c_int32, c_void_p], c_int32),
+    "qsw_destroy": ([c_void_p], None),
+    "qsw_last_error": ([c_void_p], ctypes.c_char_p),
+    "qsw_build_superoperator": ([c_void_p, POINTER(qsw_csr), POINTER(qsw_csr), c_double,
+                                 POINTER(qsw_port), c_int32, POINTER(qsw_port), c_int32, c_int32,
+                                 POINTER(c_void_p)], c_int32),
+    "qsw_set_omega": ([c_void_p, c_double], c_int32),
+    "qsw_op_info": ([c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64),
+                     POINTER(c_double)], c_int32),
+    "qsw_op_export_csr": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "qsw_op_destroy": ([c_void_p], None),
+    "qsw_initial_state": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int32),
+    "qsw_apply": ([c_void_p, c_void_p, c_void_p], c_int32),
+    "qsw_expmv_series": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p, c_void_p,
+                          POINTER(qsw_series_stats)], c_int32),
+    "qsw_expmv_series_host": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p,
+                               c_void_p, POINTER(qsw_series_stats)], c_int32),
+    "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
+    "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
+    "qsw_select_params": ([POINTER(c_double), c_double, c_int32, c_int32, POINTER(c_int32),
+                           POINTER(c_int32)], c_int32),
+}
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise QswUnavailable(f"{LIB_PATH} is not built; run `python -m "
+                                 "paper_2003_02450_gb300.build`")
+        try:
+            handle = ctypes.CDLL(LIB_PATH)
+        except OSError as exc:
+            raise QswUnavailable(str(exc)) from exc
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = handle
+    return _lib
+
+
+def _check(status: int, ctx=None):
+    if status != 0:
+        msg = lib().qsw_last_error(ctx)
+        raise QswError(status, msg.decode() if msg else "")
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return c_void_p(x)
+    if hasattr(x, "data_ptr"):
+        return c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data_as(c_void_p)
+    raise TypeError(f"cannot pass {type(x)} as a pointer")
+
+
+class _Csr:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, n, rowptr, col, w):
+        self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int32)
+        self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.w = np.ascontiguousarray(w, dtype=np.float64)
+        self.c = qsw_csr(int(n), int(self.col.size),
+                         self.rowptr.ctypes.data_as(POINTER(c_int32)),
+                         self.col.ctypes.data_as(POINTER(c_int32)),
+                         self.w.ctypes.data_as(POINTER(c_double)))
+
+
+def _as_csr(g):
+    if g is None:
+        return None
+    if hasattr(g, "rowptr"):   # workloads.Digraph
+        return _Csr(g.n, g.rowptr, g.col, g.w)
+    import scipy.sparse as sp
+    m = sp.csr_matrix(g)
+    m.sort_indices()
+    return _Csr(m.shape[0], m.indptr, m.indices, m.data)
+
+
+def _ports(ports):
+    ports = list(ports or [])
+    arr = (qsw_port * max(1, len(ports)))()
+    for k, (v, r) in enumerate(ports):
+        arr[k].vertex = int(v)
+        arr[k].rate = float(r)
+    return arr, len(ports)
+
+
+# ------------------------------------------------------------------ calls --
+
+def qsw_create(device: int = 0, stream: int | None = None):
+    h = c_void_p()
+    st = lib().qsw_create(byref(h), int(device), c_void_p(stream) if stream else None)
+    _check(st)
+    return h
+
+
+def qsw_destroy(ctx) -> None:
+    lib().qsw_destroy(ctx)
+
+
+def qsw_last_error(ctx) -> str:
+    msg = lib().qsw_last_error(ctx)
+    return msg.decode() if msg else ""
+
+
+def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(),
+                            precision="c128"):
+    g = _as_csr(G)
+    h = _as_csr(H)
+    src, nsrc = _ports(sources)
+    snk, nsnk = _ports(sinks)
+    prec = PRECISIONS.get(precision, precision)
+    op = c_void_p()
+    st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
+                                       src, nsrc, snk, nsnk, int(prec), byref(op))
+    _check(st, ctx)
+    return op
+
+
+def qsw_set_omega(ctx, op, omega: float) -> None:
+    _check(lib().qsw_set_omega(op, float(omega)), ctx)
+
+
+def qsw_op_info(ctx, op) -> dict:
+    nt, n, nnz = c_int64(), c_int64(), c_int64()
+    norms = (c_double * 9)()
+    _check(lib().qsw_op_info(op, byref(nt), byref(n), byref(nnz), norms), ctx)
+    return {"n_tilde": nt.value, "n": n.value, "nnz": nnz.value, "norms": list(norms)}
+
+
+def qsw_op_export_csr(ctx, op, d_rowptr, d_col, d_val) -> None:
+    _check(lib().qsw_op_export_csr(op, _ptr(d_rowptr), _ptr(d_col), _ptr(d_val)), ctx)
+
+
+def qsw_op_destroy(op) -> None:
+    lib().qsw_op_destroy(op)
+
+
+def qsw_initial_state(ctx, op, d_state, rho0=None, populations=None) -> None:
+    r = None if rho0 is None else np.asfortranarray(np.asarray(rho0, dtype=np.complex128))
+    p = None if populations is None else np.ascontiguousarray(populations, dtype=np.float64)
+    _check(lib().qsw_initial_state(op, _ptr(r), _ptr(p), _ptr(d_state)), ctx)
+
+
+def qsw_apply(ctx, op, d_x, d_y) -> None:
+    _check(lib().qsw_apply(op, _ptr(d_x), _ptr(d_y)), ctx)
+
+
+def qsw_expmv_series(ctx, op, d_rho0, t0: float, dt: float, steps: int, d_out=None,
+                     d_pops=None) -> dict:
+    stats = qsw_series_stats()
+    _check(lib().qsw_expmv_series(op, _ptr(d_rho0), float(t0), float(dt), int(steps),
+                                  _ptr(d_out), _ptr(d_pops), byref(stats)), ctx)
+    return stats.as_dict()
+
+
+def qsw_expmv_series_host(ctx, op, h_rho0, t0: float, dt: float, steps: int, h_out=None,
+                          h_pops=None) -> dict:
+    stats = qsw_series_stats()
+    _check(lib().qsw_expmv_series_host(op, _ptr(h_rho0), float(t0), float(dt), int(steps),
+                                       _ptr(h_out), _ptr(h_pops), byref(stats)), ctx)
+    return stats.as_dict()
+
+
+def qsw_populations(ctx, op, d_rho_series, count: int, d_pops) -> None:
+    _check(lib().qsw_populations(op, _ptr(d_rho_series), int(count), _ptr(d_pops)), ctx)
+
+
+def qsw_theta_table(precision="c128") -> np.ndarray:
+    out = (c_double * 55)()
+    _check(lib().qsw_theta_table(int(PRECISIONS.get(precision, precision)), out))
+    return np.array(out[:])
+
+
+def qsw_select_params(norms9, t: float, n0: int = 1, precision="c128"):
+    arr = (c_double * 9)(*[float(x) for x in norms9])
+    m, s = c_int32(), c_int32()
+    _check(lib().qsw_select_params(arr, float(t), int(n0), int(PRECISIONS.get(precision, precision)),
+                                   byref(m), byref(s)))
+    return m.value, s.value
