@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""Benchmark of the L-QSW time-series path on GB300.
+
+One step = one pass of the whole path over one synthetic walk: build the
+superoperator from the host graph (normalisation, CSR assembly, 1-norm series),
+run the Al-Mohy--Higham series on the device (parameter choice, Taylor blocks,
+populations).  Default workload: Erdos-Renyi digraph N = 1000, p = 0.01,
+weights U(0.5, 1.5), omega = 0.3, uniform-superposition rho0, complex128,
+50 steps of dt = 0.1 (superoperator 10^6 rows, ~4.07e7 nnz).
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Metric: walk time-steps/s (output times of the series per second, whole job).
+Walks are independent, so N > 1 runs one walk per rank (weak scaling, no
+collective on the data path).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "walk time-steps/s (L-QSW expmv series, whole path incl. superoperator build)"
+UNIT = "time-steps/s"
+WORKLOAD = "er1000"
+SAMPLE_STEPS = 2   # output times of the oracle sample
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--operator", default="matfree", choices=["matfree", "csr"],
+                    help="how the series applies the superoperator")
+    ap.add_argument("--no-csr-line", action="store_true",
+                    help="skip the extra CSR-operator series measurement")
+    ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--profile-steps", type=int, default=0,
+                    help="run one build + one series of this many output times and exit "
+                         "(small case for ncu captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ------------------------------------------------------------------ oracle --
+
+def oracle_sample() -> dict:
+    """Oracle as it stands on the ER-1000 workload: Kronecker assembly plus
+    Algorithm 5.2 over the first SAMPLE_STEPS output times."""
+    from oracle import expmv, graph, superop
+    from paper_2003_02450_gb300 import workloads as W
+    cfg = W.er1000()
+    t = time.perf_counter()
+    walk = graph.lqsw_walk(graph.adjacency(cfg.graph))
+    L = superop.superoperator(walk, cfg.omega)
+    X = expmv.expmv_series(L, W.vec(cfg.rho0), cfg.t0, cfg.dt, SAMPLE_STEPS)
+    superop.populations(X, walk.n_tilde)
+    sec = time.perf_counter() - t
+    return {"seconds": sec, "steps": SAMPLE_STEPS}
+
+
+def run_oracle_subprocess() -> dict:
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"],
+                         capture_output=True, text=True, env=env, cwd=ROOT)
+    if res.returncode != 0:
+        raise RuntimeError("oracle sample failed:\n" + res.stderr[-2000:])
+    return json.loads(res.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_block(sample: dict) -> dict:
+    return {"value": sample["steps"] / sample["seconds"], "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "sample": (f"FP64 numpy/scipy oracle, single thread: Kronecker-product superoperator "
+                       f"of the ER-1000 walk + Algorithm 5.2 over its first {sample['steps']} "
+                       f"output times (dt=0.1), {sample['seconds']:.1f} s")}
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# -------------------------------------------------------------------- ours --
+
+def measured_peak_gbs():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+# FP64 FMA issue rate of GB300: 304 thread-FMAs per cycle for the whole GPU
+# (2 per SM per clock; ncu sm__sass_thread_inst_executed_op_dfma_pred_on
+# .sum.peak_sustained), 2 flops each, at the maximum SM clock.
+DFMA_PER_CYCLE = 304
+
+
+def fp64_peak_tflops():
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            mhz = float(json.load(fh).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return DFMA_PER_CYCLE * 2 * mhz * 1e6 / 1e12
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+
+    rank, world, local_rank = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    cfg = W.er1000()
+    N, n, q = cfg.graph.n, cfg.graph.n ** 2, cfg.steps
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(local_rank, stream.cuda_stream)
+    rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
+    out = torch.empty((q + 1, n), dtype=torch.complex128, device=dev)
+    pops = torch.empty((q + 1, N), dtype=torch.float64, device=dev)
+
+    def one_step():
+        op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision="c128",
+                                       operator=args.operator)
+        st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, pops)
+        info = C.qsw_op_info(ctx, op)
+        C.qsw_op_destroy(op)
+        st["nnz"] = info["nnz"]
+        return st
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    l0 = C.qsw_kernel_launches()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    stats = [one_step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    launches = (C.qsw_kernel_launches() - l0) / args.steps
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * q * 1000.0 / ms
+
+    kern_ms = statistics.mean(s["kernel_ms"] for s in stats)
+    alg_bytes = statistics.mean(s["algorithmic_bytes"] for s in stats)
+    alg_flops = statistics.mean(s["algorithmic_flops"] for s in stats)
+    peak, peak_kind = measured_peak_gbs()
+    achieved = alg_bytes / (kern_ms * 1e-3) / 1e9
+    fp64_peak = fp64_peak_tflops()
+    achieved_tf = alg_flops / (kern_ms * 1e-3) / 1e12
+    s0 = stats[0]
+
+    # ---- the CSR-operator series on the same walk (secondary line)
+    csr_line = None
+    if not args.no_csr_line:
+        op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision="c128",
+                                       operator="csr")
+        C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, pops)
+        cs = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, pops)
+        C.qsw_op_destroy(op)
+        csr_line = {"kernel_ms": cs["kernel_ms"], "matvecs": cs["matvecs"],
+                    "bytes_per_matvec": cs["bytes_per_matvec"],
+                    "achieved_gbs": cs["algorithmic_bytes"] / (cs["kernel_ms"] * 1e-3) / 1e9,
+                    "achieved_tflops_fp64": cs["algorithmic_flops"] / (cs["kernel_ms"] * 1e-3) / 1e12,
+                    "series_time_steps_per_s": q * 1000.0 / cs["kernel_ms"]}
+
+    # ---- end to end through the host-buffer entry point
+    e2e = None
+    if not args.no_e2e:
+        h_rho0 = torch.from_numpy(W.vec(cfg.rho0)).pin_memory()
+        h_out = torch.empty((q + 1, n), dtype=torch.complex128).pin_memory()
+        h_pops = torch.empty((q + 1, N), dtype=torch.float64).pin_memory()
+
+        def e2e_step():
+            op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision="c128",
+                                           operator=args.operator)
+            C.qsw_expmv_series_host(ctx, op, h_rho0, cfg.t0, cfg.dt, q, h_out, h_pops)
+            C.qsw_op_destroy(op)
+
+        for _ in range(max(1, args.warmup)):
+            e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize(dev)
+        e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
+        if world > 1:
+            import torch.distributed as dist
+            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        g = cfg.graph
+        h2d = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + h_rho0.numel() * 16
+        d2h = h_out.numel() * 16 + h_pops.numel() * 8
+        e2e = {"value": world * q * 1000.0 / e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms,
+               "api": "qsw_build_superoperator + qsw_expmv_series_host (host buffers)"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            cpu = cpu_baseline_block(run_oracle_subprocess())
+        except Exception as exc:   # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)[:300]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128 (complex128 / FP64)",
+            "data": "synthetic (seeded Erdos-Renyi digraph; the paper's graph sets are not available)",
+            "config": {"workload": WORKLOAD, "graph": "Erdos-Renyi digraph N=1000 p=0.01 w~U(0.5,1.5)",
+                       "omega": cfg.omega, "rho0": "uniform superposition (dense)",
+                       "t0": cfg.t0, "dt": cfg.dt, "series_steps": q, "rows": n, "nnz": s0["nnz"],
+                       "parallelism": f"replicas x{world} (one walk per GPU)",
+                       "l2": "inputs larger than L2 (CSR 0.81 GB streamed every matvec)"},
+            "roofline": {"bound": "alu", "pipe": "fp64",
+                         "kernel": f"series_kernel ({args.operator} operator, fused Taylor update)",
+                         "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": achieved_tf / fp64_peak,
+                         "peak_source": "304 DFMA/cycle x 2 flop x max SM clock (ncu peak_sustained)",
+                         "traffic": None, "algorithmic_flops_per_launch": alg_flops,
+                         "kernel_ms": kern_ms,
+                         "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
+                                      "frac": achieved / peak, "peak_source": peak_kind,
+                                      "algorithmic_bytes_per_launch": alg_bytes}},
+            "csr_operator_series": csr_line,
+            "series": {"m_star": s0["m_star"], "s": s0["s"], "outputs_per_block": s0["outputs_per_block"],
+                       "matvecs": s0["matvecs"], "bytes_per_matvec": s0["bytes_per_matvec"],
+                       "series_time_steps_per_s": q * 1000.0 / kern_ms,
+                       "build_and_other_ms": ms - kern_ms},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    C.qsw_destroy(ctx)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# --------------------------------------------------------------- reference --
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    for _ in range(min(args.warmup, 1)):   # one untimed sample: page in numpy/scipy
+        run_oracle_subprocess()
+    samples = [run_oracle_subprocess() for _ in range(args.steps)]
+    sec = sum(s["seconds"] for s in samples)
+    steps = sum(s["steps"] for s in samples)
+    value = steps / sec
+    cpu = cpu_baseline_block({"seconds": sec / len(samples), "steps": SAMPLE_STEPS})
+    cpu["value"] = value
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * sec / len(samples),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c128 (complex128 / FP64)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_output_times": SAMPLE_STEPS},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_profile_case(q: int):
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    cfg = W.er1000()
+    dev = torch.device("cuda", 0)
+    ctx = C.qsw_create(0, torch.cuda.current_stream(dev).cuda_stream)
+    rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
+    out = torch.empty((q + 1, cfg.graph.n ** 2), dtype=torch.complex128, device=dev)
+    op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega)
+    st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, None)
+    C.qsw_op_destroy(op)
+    C.qsw_destroy(ctx)
+    print(json.dumps({"profile_case": WORKLOAD, "series_steps": q, "matvecs": st["matvecs"],
+                      "kernel_ms": st["kernel_ms"], "algorithmic_bytes": st["algorithmic_bytes"]}))
+
+
+def main():
+    args = parse_args()
+    if args.profile_steps:
+        run_profile_case(args.profile_steps)
+        return
+    if args.oracle_sample:
+        print(json.dumps(oracle_sample()))
+        return
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -65,6 +65,14 @@ typedef enum {
  *   tolerance 2^-24 with its own theta table.  Not in the paper. */
 typedef enum { QSW_C128 = 0, QSW_C64_BULK = 1 } qsw_precision;
 
+/* How the series applies L~.
+ * QSW_OPERATOR_MATRIX_FREE (default): from H and the jump lists directly
+ *   (Eq. vec_mappings applied to Eq. qsw_ss), no stored superoperator; every
+ *   term is a real coefficient times a complex entry.  Same operator as the CSR
+ *   entry by entry; only the summation order differs.
+ * QSW_OPERATOR_CSR: the assembled CSR superoperator (Section 3.2-3.3). */
+typedef enum { QSW_OPERATOR_MATRIX_FREE = 0, QSW_OPERATOR_CSR = 1 } qsw_operator;
+
 typedef struct qsw_ctx qsw_ctx;   /* device + stream + workspace cache */
 typedef struct qsw_op qsw_op;     /* one assembled superoperator L~ */
 
@@ -94,7 +102,19 @@ typedef struct {
   int32_t jobs;              /* Taylor blocks executed */
   int64_t matvecs;           /* applications of L~ performed */
   double bytes_per_matvec;   /* algorithmic bytes of one application of L~ */
-  double kernel_ms;          /* device time of the series kernel */
+  double kernel_ms;          /* device time of the series kernel (CUDA events) */
+  int64_t fupdates;          /* sum over Taylor terms of the outputs updated */
+  double algorithmic_bytes;  /* bytes the series kernel must move: matvecs x
+                                bytes_per_matvec + 32 n fupdates + block inits */
+  double algorithmic_flops;  /* FP64 (QSW_C128) or FP32 + FP64 (QSW_C64_BULK)
+                                flops of the series: per application of L~,
+                                4 per real x complex off-diagonal term, 8 per
+                                diagonal term, 4 per jump term, 2 per scaling,
+                                3 per squared modulus; per updated output
+                                element 4 + 3 */
+  int32_t hermitian;         /* 1: rho0 was Hermitian and the matrix-free form
+                                computed upper triangles only (every Taylor
+                                term of a Hermitian matrix is Hermitian) */
 } qsw_series_stats;
 
 /* ---------------------------------------------------------------- context */
@@ -122,6 +142,9 @@ const char* qsw_last_error(const qsw_ctx* ctx);
  *   omega    : decoherence parameter in [0, 1] (Eq. qsw).
  *   sources, n_sources, sinks, n_sinks : ports (may be NULL when the count is 0).
  *   precision: a qsw_precision.
+ *   operator_kind: a qsw_operator.  With QSW_OPERATOR_CSR the CSR is assembled
+ *              here; with QSW_OPERATOR_MATRIX_FREE it is assembled only if
+ *              qsw_op_export_csr asks for it.
  * On success *out receives a library-owned operator (free with
  * qsw_op_destroy).  Construction also precomputes ||L~||_1 exactly and
  * estimates ||L~^p||_1 for p = 2..9 (Section 4 footnote) on the device.
@@ -130,7 +153,7 @@ const char* qsw_last_error(const qsw_ctx* ctx);
 qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H,
                                    double omega, const qsw_port* sources, int32_t n_sources,
                                    const qsw_port* sinks, int32_t n_sinks,
-                                   int32_t precision, qsw_op** out);
+                                   int32_t precision, int32_t operator_kind, qsw_op** out);
 
 /* Rebuild the values and the 1-norm series of `op` at a new omega, keeping
  * its graph, Hamiltonian and ports (the package's set_omega, Section 4). */
@@ -140,8 +163,11 @@ qsw_status qsw_set_omega(qsw_op* op, double omega);
  * estimate of ||L~^p||_1 for p = 2..9.  Any output pointer may be NULL. */
 qsw_status qsw_op_info(const qsw_op* op, int64_t* n_tilde, int64_t* n, int64_t* nnz,
                        double* norms9);
+/* nnz is the number of stored entries of the CSR form of L~ (computed from the
+ * structure without assembling it). */
 
-/* Copy the assembled CSR of L~ into caller device buffers: d_rowptr[n + 1],
+/* Copy the CSR of L~ (assembled on first use for a matrix-free operator) into
+ * caller device buffers: d_rowptr[n + 1],
  * d_col[nnz], d_val[2 nnz] (complex128; for a QSW_C64_BULK operator its
  * complex64 values are widened).  Any pointer may be NULL to skip that array.
  * Used by tests and tools. */
@@ -194,6 +220,10 @@ qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t
                            double* d_pops);
 
 /* ----------------------------------------------------- host-side helpers */
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * (all contexts), for launch accounting.  Pure host call. */
+int64_t qsw_kernel_launches(void);
 
 /* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
  * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor

@@ -15,6 +15,8 @@
 using qsw::Error;
 using qsw::Op;
 
+std::atomic<long long> qsw::g_launches{0};
+
 namespace {
 
 thread_local std::string g_orphan_error;
@@ -87,14 +89,19 @@ void check_ports(const qsw_port* p, int count, int N, const char* name) {
 
 void rebuild(Op& op) {
   qsw::build_jumps(op);
-  qsw::Csr LH;
+  qsw::prep_matfree(op);
   op.L = qsw::Csr{};
-  qsw::assemble(op, false, op.L);
-  qsw::assemble(op, true, LH);
-  qsw::compute_norms(op, op.L, LH);
-  LH = qsw::Csr{};
-  if (op.precision == QSW_C64_BULK) qsw::to_fp32(op, op.L);
-  op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
+  if (op.opkind == QSW_OPERATOR_CSR) {
+    qsw::Csr LH;
+    qsw::assemble(op, false, op.L);
+    qsw::assemble(op, true, LH);
+    qsw::compute_norms(op, &op.L, &LH);
+    LH = qsw::Csr{};
+    if (op.precision == QSW_C64_BULK) qsw::to_fp32(op, op.L);
+    op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
+  } else {
+    qsw::compute_norms(op, nullptr, nullptr);
+  }
 }
 
 }  // namespace
@@ -136,7 +143,7 @@ const char* qsw_last_error(const qsw_ctx* ctx) {
 qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, double omega,
                                    const qsw_port* sources, int32_t n_sources,
                                    const qsw_port* sinks, int32_t n_sinks, int32_t precision,
-                                   qsw_op** out) {
+                                   int32_t operator_kind, qsw_op** out) {
   return guarded(ctx, [&] {
     QSW_CHECK_ARG(ctx != nullptr && out != nullptr, QSW_ERR_INVALID_ARG, "ctx/out is NULL");
     *out = nullptr;
@@ -147,6 +154,8 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
                   "omega must lie in [0, 1]");
     QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
                   "unknown precision");
+    QSW_CHECK_ARG(operator_kind == QSW_OPERATOR_MATRIX_FREE || operator_kind == QSW_OPERATOR_CSR,
+                  QSW_ERR_INVALID_ARG, "unknown operator kind");
     if (H) {
       check_csr(H, "H", true);
       QSW_CHECK_ARG(H->n == G->n, QSW_ERR_INVALID_ARG, "H must be N x N");
@@ -167,6 +176,7 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
     std::unique_ptr<Op> op(new Op());
     op->ctx = ctx;
     op->precision = precision;
+    op->opkind = operator_kind;
     op->omega = omega;
     op->N = G->n;
     op->Nt = (int)Nt;
@@ -213,7 +223,7 @@ qsw_status qsw_op_info(const qsw_op* h, int64_t* n_tilde, int64_t* n, int64_t* n
     QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
     if (n_tilde) *n_tilde = op->Nt;
     if (n) *n = op->n;
-    if (nnz) *nnz = op->L.nnz;
+    if (nnz) *nnz = op->nnz_csr;
     if (norms9) memcpy(norms9, op->norms, sizeof(double) * qsw::kNormPowers);
   });
 }
@@ -224,15 +234,21 @@ qsw_status qsw_op_export_csr(const qsw_op* h, int32_t* d_rowptr, int32_t* d_col,
     QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
     set_device(op->ctx);
     cudaStream_t st = op->ctx->stream;
+    qsw::Csr tmp;
+    const qsw::Csr* L = &op->L;
+    if (op->opkind != QSW_OPERATOR_CSR) {   // assemble on demand, FP64
+      qsw::assemble(*const_cast<Op*>(op), false, tmp);
+      L = &tmp;
+    }
     if (d_rowptr)
-      QSW_CUDA_TRY(cudaMemcpyAsync(d_rowptr, op->L.rowptr.p, sizeof(int) * (op->n + 1),
+      QSW_CUDA_TRY(cudaMemcpyAsync(d_rowptr, L->rowptr.p, sizeof(int) * (op->n + 1),
                                    cudaMemcpyDeviceToDevice, st));
     if (d_col)
-      QSW_CUDA_TRY(cudaMemcpyAsync(d_col, op->L.col.p, sizeof(int) * op->L.nnz,
+      QSW_CUDA_TRY(cudaMemcpyAsync(d_col, L->col.p, sizeof(int) * L->nnz,
                                    cudaMemcpyDeviceToDevice, st));
     if (d_val) {
-      if (!op->L.fp32) {
-        QSW_CUDA_TRY(cudaMemcpyAsync(d_val, op->L.val.p, sizeof(double2) * op->L.nnz,
+      if (!L->fp32) {
+        QSW_CUDA_TRY(cudaMemcpyAsync(d_val, L->val.p, sizeof(double2) * L->nnz,
                                      cudaMemcpyDeviceToDevice, st));
       } else {
         qsw::widen_values(*op, d_val);
@@ -348,6 +364,8 @@ qsw_status qsw_populations(const qsw_op* h, const double* d_rho, int32_t count, 
     qsw::populations(*op, d_rho, count, d_pops);
   });
 }
+
+int64_t qsw_kernel_launches(void) { return qsw::g_launches.load(); }
 
 qsw_status qsw_theta_table(int32_t precision, double* theta55) {
   return guarded(nullptr, [&] {

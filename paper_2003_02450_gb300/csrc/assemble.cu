@@ -186,12 +186,12 @@ void assemble(Op& op, bool adjoint, Csr& out) {
   prefoff.alloc(sizeof(long long) * (Nt + 1));
   blen.alloc(sizeof(long long) * (Nt + 1));
   bstart.alloc(sizeof(long long) * (Nt + 1));
-  block_lengths_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(a, offc.as<long long>(), nullptr);
-  scan_small_t<long long><<<1, 1024, 0, st>>>(offc.as<long long>(), prefoff.as<long long>(), Nt);
+  QSW_LAUNCH block_lengths_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(a, offc.as<long long>(), nullptr);
+  QSW_LAUNCH scan_small_t<long long><<<1, 1024, 0, st>>>(offc.as<long long>(), prefoff.as<long long>(), Nt);
   a.prefoff = prefoff.as<long long>();
-  block_lengths_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(a, offc.as<long long>(),
+  QSW_LAUNCH block_lengths_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(a, offc.as<long long>(),
                                                                 blen.as<long long>());
-  scan_small_t<long long><<<1, 1024, 0, st>>>(blen.as<long long>(), bstart.as<long long>(), Nt);
+  QSW_LAUNCH scan_small_t<long long><<<1, 1024, 0, st>>>(blen.as<long long>(), bstart.as<long long>(), Nt);
   QSW_CUDA_TRY(cudaGetLastError());
   long long nnz = 0;
   QSW_CUDA_TRY(cudaMemcpyAsync(&nnz, bstart.as<long long>() + Nt, sizeof(long long),
@@ -208,7 +208,7 @@ void assemble(Op& op, bool adjoint, Csr& out) {
   a.rowptr = out.rowptr.as<int>();
   a.col = out.col.as<int>();
   a.val = out.val.as<double2>();
-  assemble_kernel<<<grid_for(a.n, 256, 152 * 64), 256, 0, st>>>(a);
+  QSW_LAUNCH assemble_kernel<<<grid_for(a.n, 256, 152 * 64), 256, 0, st>>>(a);
   QSW_CUDA_TRY(cudaGetLastError());
   QSW_CUDA_TRY(cudaStreamSynchronize(st));   // scratch buffers die at scope exit
 }
@@ -218,7 +218,7 @@ void to_fp32(Op& op, Csr& m) {
   cudaStream_t st = op.ctx->stream;
   DevBuf v32;
   v32.alloc(sizeof(float2) * (m.nnz + 1));
-  narrow_kernel<<<grid_for(m.nnz, 256, 152 * 64), 256, 0, st>>>(m.nnz, m.val.as<double2>(),
+  QSW_LAUNCH narrow_kernel<<<grid_for(m.nnz, 256, 152 * 64), 256, 0, st>>>(m.nnz, m.val.as<double2>(),
                                                                  v32.as<float2>());
   QSW_CUDA_TRY(cudaGetLastError());
   QSW_CUDA_TRY(cudaStreamSynchronize(st));

@@ -15,6 +15,8 @@
 //
 // All lists come out sorted by column, and every floating-point sum is taken
 // in ascending index order, so the results are deterministic.
+#include <algorithm>
+
 #include "op.h"
 
 namespace qsw {
@@ -231,6 +233,36 @@ __global__ void row_sum_kernel(int n, const int* __restrict__ rowptr, const doub
   }
 }
 
+__global__ void prep_mf_kernel(int N, int Nt, double omw, const int* __restrict__ hrow,
+                               const double* __restrict__ hval, int nnz_h, double* hval64,
+                               float* hval32, const double* __restrict__ hdiag,
+                               const double* __restrict__ dtot, double* ad64, float* ad32,
+                               double* hw64, float* hw32, double* habs,
+                               const double* __restrict__ jval, float* jval32, int nj,
+                               const double* __restrict__ jtval, float* jtval32, int njt) {
+  const int t0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const int nth = gridDim.x * blockDim.x;
+  for (int e = t0; e < nnz_h; e += nth) {
+    const double v = omw * hval[e];
+    hval64[e] = v;
+    hval32[e] = (float)v;
+  }
+  for (int v = t0; v < Nt; v += nth) {
+    const double a = -0.5 * dtot[v];
+    const double h = omw * hdiag[v];
+    ad64[v] = a;
+    ad32[v] = (float)a;
+    hw64[v] = h;
+    hw32[v] = (float)h;
+    double s = 0.0;
+    if (v < N)
+      for (int e = hrow[v]; e < hrow[v + 1]; ++e) s += fabs(omw * hval[e]);
+    habs[v] = s;
+  }
+  for (int e = t0; e < nj; e += nth) jval32[e] = (float)jval[e];
+  for (int e = t0; e < njt; e += nth) jtval32[e] = (float)jtval[e];
+}
+
 template <class T>
 void upload(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
   b.alloc(sizeof(T) * (h.size() ? h.size() : 1));
@@ -248,7 +280,7 @@ int read_int(const int* d, cudaStream_t st) {
 // cnt[0..n) -> rowptr[0..n]; returns the total.
 int scan_counts(DevBuf& cnt, DevBuf& rowptr, int n, cudaStream_t st) {
   rowptr.alloc(sizeof(int) * (n + 1));
-  scan_small_kernel<<<1, 1024, 0, st>>>(cnt.as<int>(), rowptr.as<int>(), n);
+  QSW_LAUNCH scan_small_kernel<<<1, 1024, 0, st>>>(cnt.as<int>(), rowptr.as<int>(), n);
   QSW_CUDA_TRY(cudaGetLastError());
   return read_int(rowptr.as<int>() + n, st);
 }
@@ -276,17 +308,17 @@ void build_graph(Op& op) {
   g.scratch.alloc(sizeof(int) * (g.Nt + 1));
   QSW_CUDA_TRY(cudaMemsetAsync(g.scratch.p, 0, sizeof(int) * (N + 1), st));
   if (g.nnz_g)
-    count_cols_kernel<<<grid_for(g.nnz_g, 256, 4096), 256, 0, st>>>(g.nnz_g, g.g_col.as<int>(),
+    QSW_LAUNCH count_cols_kernel<<<grid_for(g.nnz_g, 256, 4096), 256, 0, st>>>(g.nnz_g, g.g_col.as<int>(),
                                                                      g.scratch.as<int>());
   scan_counts(g.scratch, g.gt_rowptr, N, st);
   g.gt_col.alloc(sizeof(int) * (g.nnz_g + 1));
   g.gt_w.alloc(sizeof(double) * (g.nnz_g + 1));
   QSW_CUDA_TRY(cudaMemcpyAsync(g.scratch.p, g.gt_rowptr.p, sizeof(int) * N,
                                cudaMemcpyDeviceToDevice, st));
-  scatter_transpose_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+  QSW_LAUNCH scatter_transpose_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
       N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.g_w.as<double>(), g.scratch.as<int>(),
       g.gt_col.as<int>(), g.gt_w.as<double>());
-  sort_segments_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, g.gt_rowptr.as<int>(),
+  QSW_LAUNCH sort_segments_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, g.gt_rowptr.as<int>(),
                                                                g.gt_col.as<int>(), g.gt_w.as<double>());
   QSW_CUDA_TRY(cudaGetLastError());
 
@@ -294,13 +326,13 @@ void build_graph(Op& op) {
   g.hdiag.alloc(sizeof(double) * g.Nt);
   QSW_CUDA_TRY(cudaMemsetAsync(g.hdiag.p, 0, sizeof(double) * g.Nt, st));
   if (!op.h_given) {
-    union_count_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+    QSW_LAUNCH union_count_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
         N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.gt_rowptr.as<int>(), g.gt_col.as<int>(),
         g.scratch.as<int>());
     g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
-    laplacian_fill_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+    QSW_LAUNCH laplacian_fill_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
         N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.g_w.as<double>(), g.gt_rowptr.as<int>(),
         g.gt_col.as<int>(), g.gt_w.as<double>(), g.hoff_rowptr.as<int>(), g.hoff_col.as<int>(),
         g.hoff_val.as<double>(), g.hdiag.as<double>());
@@ -309,12 +341,12 @@ void build_graph(Op& op) {
     upload(hr, op.h_rowptr, st);
     upload(hc, op.h_col, st);
     upload(hw, op.h_w, st);
-    h_offcount_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, hr.as<int>(), hc.as<int>(),
+    QSW_LAUNCH h_offcount_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, hr.as<int>(), hc.as<int>(),
                                                                g.scratch.as<int>());
     g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
-    h_split_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
+    QSW_LAUNCH h_split_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
         N, hr.as<int>(), hc.as<int>(), hw.as<double>(), g.hoff_rowptr.as<int>(),
         g.hoff_col.as<int>(), g.hoff_val.as<double>(), g.hdiag.as<double>());
     QSW_CUDA_TRY(cudaStreamSynchronize(st));   // hr/hc/hw die at scope exit
@@ -336,21 +368,49 @@ void build_jumps(Op& op) {
     const int* grow = adjoint ? g.gt_rowptr.as<int>() : g.g_rowptr.as<int>();
     const int* gcol = adjoint ? g.gt_col.as<int>() : g.g_col.as<int>();
     const double* gw = adjoint ? g.gt_w.as<double>() : g.g_w.as<double>();
-    jump_count_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, grow,
+    QSW_LAUNCH jump_count_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, grow,
                                                                g.scratch.as<int>(), adjoint);
     QSW_CUDA_TRY(cudaGetLastError());
     const int total = scan_counts(g.scratch, rp, Nt, st);
     cl.alloc(sizeof(int) * (total + 1));
     vl.alloc(sizeof(double) * (total + 1));
-    jump_fill_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, op.omega, grow, gcol,
+    QSW_LAUNCH jump_fill_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, op.omega, grow, gcol,
                                                               gw, rp.as<int>(), cl.as<int>(),
                                                               vl.as<double>(), adjoint);
     QSW_CUDA_TRY(cudaGetLastError());
   }
+  g.n_jumps = read_int(g.j_rowptr.as<int>() + Nt, st);
   g.dtot.alloc(sizeof(double) * Nt);
-  row_sum_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(Nt, g.jt_rowptr.as<int>(),
+  QSW_LAUNCH row_sum_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(Nt, g.jt_rowptr.as<int>(),
                                                           g.jt_val.as<double>(), g.dtot.as<double>());
   QSW_CUDA_TRY(cudaGetLastError());
+}
+
+void prep_matfree(Op& op) {
+  cudaStream_t st = op.ctx->stream;
+  GraphDev& g = op.g;
+  MfData& m = op.mf;
+  const int Nt = g.Nt, nh = std::max(1, g.nnz_hoff), nj = std::max(1, g.n_jumps);
+  m.hval64.alloc(sizeof(double) * nh);
+  m.hval32.alloc(sizeof(float) * nh);
+  m.ad64.alloc(sizeof(double) * Nt);
+  m.ad32.alloc(sizeof(float) * Nt);
+  m.hw64.alloc(sizeof(double) * Nt);
+  m.hw32.alloc(sizeof(float) * Nt);
+  m.habs.alloc(sizeof(double) * Nt);
+  m.jval32.alloc(sizeof(float) * nj);
+  m.jtval32.alloc(sizeof(float) * nj);
+  const double omw = 1.0 - op.omega;
+  QSW_LAUNCH prep_mf_kernel<<<grid_for(std::max(g.nnz_hoff, Nt), 256, 1024), 256, 0, st>>>(
+      g.N, Nt, omw, g.hoff_rowptr.as<int>(), g.hoff_val.as<double>(), g.nnz_hoff,
+      m.hval64.as<double>(), m.hval32.as<float>(), g.hdiag.as<double>(), g.dtot.as<double>(),
+      m.ad64.as<double>(), m.ad32.as<float>(), m.hw64.as<double>(), m.hw32.as<float>(),
+      m.habs.as<double>(), g.j_val.as<double>(), m.jval32.as<float>(), g.n_jumps,
+      g.jt_val.as<double>(), m.jtval32.as<float>(), g.n_jumps);
+  QSW_CUDA_TRY(cudaGetLastError());
+  // entries of the CSR form: diagonal + commutator stripes/blocks + one per jump
+  const long long n = (long long)Nt * Nt;
+  op.nnz_csr = n + (op.omega < 1.0 ? 2LL * Nt * g.nnz_hoff : 0LL) + g.n_jumps;
 }
 
 }  // namespace qsw

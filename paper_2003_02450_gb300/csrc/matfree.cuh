@@ -1,0 +1,147 @@
+// Matrix-free application of the L-QSW superoperator (no CSR): the action of
+// Eq. qsw_ss on a vectorised rho, written with the identities of
+// Eq. vec_mappings so that every term is a product of a REAL coefficient and a
+// complex entry of rho:
+//
+//   (L~ x)_(i,j) = -i C_ij + D_ij x_ij + [i = j] sum_q r_iq x_(q,q)
+//   C_ij  = sum_{m != i} c_im x_(m,j)  -  sum_{m != j} x_(i,m) c_mj,   c = (1 - omega) H
+//   D_ij  = -(dtot_i + dtot_j)/2 - i (1 - omega)(H_ii - H_jj)
+//
+// (r_iq the jump rates, dtot_v the total rate leaving v).  The adjoint L~^H
+// (used by the 1-norm estimator) is  +i C_ij + conj(D_ij) x_ij + jumps of the
+// transposed list.  This is the same operator the CSR assembly stores, entry by
+// entry; only the summation order differs.
+//
+// On GB300 the FP64 pipe issues 2 FMA per SM per clock, so the complex128 form
+// is bound by FP64 issue, not by HBM: each off-diagonal term costs the minimum
+// of 2 FMA (real x complex), there are no cross-lane FP64 reductions (one thread
+// owns one element), and no matrix is streamed from memory.
+#pragma once
+
+#include "qsw_internal.h"
+
+namespace qsw {
+
+template <class R> struct MfOp {
+  int N, Nt;           // N: vertices that have Hamiltonian rows (0 when omega = 1)
+  const int* hrow;     // [N + 1] off-diagonal H, rows of the graph vertices
+  const int* hcol;
+  const R* hval;       // (1 - omega) H_im
+  const R* ad;         // [Nt] -dtot_v / 2
+  const R* hw;         // [Nt] (1 - omega) H_vv
+  const int* jrow;     // [Nt + 1] jumps into i (L) or out of i (L^H)
+  const int* jcol;
+  const R* jval;
+};
+
+template <class T> __device__ __forceinline__ T ldcg_t(const T* p) { return __ldcg(p); }
+
+// Entry (a, b) of x.  With HERM the array holds only its upper triangle
+// (a <= b) of a Hermitian matrix and (a, b), a > b, is read as conj(x(b, a)).
+template <bool HERM, class VT>
+__device__ __forceinline__ VT mf_ld(const VT* __restrict__ x, int Nt, int a, int b) {
+  if (!HERM) return __ldcg(x + a + (long long)Nt * b);
+  const bool up = a <= b;
+  VT v = __ldcg(x + (up ? a : b) + (long long)Nt * (up ? b : a));
+  if (!up) v.y = -v.y;
+  return v;
+}
+
+// Part B of C for RPT rows of one column: sum over the uniform list H row j.
+template <class R, class VT, int RPT, bool HERM>
+__device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict__ x, int j,
+                                         const int* irow, R* bx, R* by) {
+#pragma unroll
+  for (int u = 0; u < RPT; ++u) { bx[u] = 0; by[u] = 0; }
+  if (j >= op.N) return;
+  const int e0 = op.hrow[j], e1 = op.hrow[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const int m = op.hcol[e];
+    const R h = op.hval[e];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      if (irow[u] >= 0) {
+        const VT v = mf_ld<HERM>(x, op.Nt, irow[u], m);
+        bx[u] = fma(h, v.x, bx[u]);
+        by[u] = fma(h, v.y, by[u]);
+      }
+    }
+  }
+}
+
+// The rest of element (i, j): part A, diagonal, jumps; returns (L x)_(i,j) or
+// (L^H x)_(i,j) given part B.
+template <class R, class VT, bool ADJ, bool HERM>
+__device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
+                                          R bx, R by, R& yx, R& yy) {
+  R ax = 0, ay = 0;
+  if (i < op.N) {
+    const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const VT v = mf_ld<HERM>(x, op.Nt, op.hcol[e], j);
+      const R h = op.hval[e];
+      ax = fma(h, v.x, ax);
+      ay = fma(h, v.y, ay);
+    }
+  }
+  const R cx = ax - bx, cy = ay - by;
+  const VT xs = __ldcg(x + i + (long long)op.Nt * j);
+  const R dx = op.ad[i] + op.ad[j];
+  const R dy = op.hw[j] - op.hw[i];
+  R rx, ry;
+  if (!ADJ) {   // -i C + D x
+    rx = fma(dx, xs.x, fma(-dy, xs.y, cy));
+    ry = fma(dx, xs.y, fma(dy, xs.x, -cx));
+  } else {      // +i C + conj(D) x
+    rx = fma(dx, xs.x, fma(dy, xs.y, -cy));
+    ry = fma(dx, xs.y, fma(-dy, xs.x, cx));
+  }
+  if (i == j) {
+    const int e0 = op.jrow[i], e1 = op.jrow[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const VT v = __ldcg(x + (long long)op.jcol[e] * (op.Nt + 1));
+      const R r = op.jval[e];
+      rx = fma(r, v.x, rx);
+      ry = fma(r, v.y, ry);
+    }
+  }
+  yx = rx;
+  yy = ry;
+}
+
+// Work items of one matrix-free pass: 64-row chunks of the columns j.  In the
+// Hermitian form only rows i <= j are computed, so column j has
+// floor(j / 64) + 1 chunks and the items before column j number
+// P(j) = j + 64 a(a-1)/2 + a b  (j = 64 a + b).
+constexpr int kItemRows = 64;
+
+__device__ __forceinline__ long long herm_items_before(int j) {
+  const long long a = j / kItemRows, b = j % kItemRows;
+  return j + kItemRows * a * (a - 1) / 2 + a * b;
+}
+
+__host__ __device__ inline long long mf_item_count(int Nt, bool herm) {
+  if (!herm) return (long long)Nt * ((Nt + kItemRows - 1) / kItemRows);
+  const long long a = Nt / kItemRows, b = Nt % kItemRows;
+  return Nt + kItemRows * a * (a - 1) / 2 + a * b;
+}
+
+// item -> (column j, first row i0)
+__device__ __forceinline__ void mf_item(long long k, int Nt, bool herm, int& j, int& i0) {
+  if (!herm) {
+    const int cpc = (Nt + kItemRows - 1) / kItemRows;
+    j = (int)(k / cpc);
+    i0 = (int)(k % cpc) * kItemRows;
+    return;
+  }
+  int lo = 0, hi = Nt - 1;   // largest j with herm_items_before(j) <= k
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (herm_items_before(mid) <= k) lo = mid;
+    else hi = mid - 1;
+  }
+  j = lo;
+  i0 = (int)(k - herm_items_before(lo)) * kItemRows;
+}
+
+}  // namespace qsw

@@ -39,7 +39,7 @@ __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed
   return z ^ (z >> 31);
 }
 
-// Y[n x t] = A X[n x t], row-major blocks, one 8-lane group per row.
+// Y = A X for t column vectors stored n apart (CSR operator), 8 lanes per row.
 __global__ void spmm_kernel(int n, int t, const int* __restrict__ rowptr, const int* __restrict__ col,
                             const double2* __restrict__ val, const double2* __restrict__ X,
                             double2* __restrict__ Y) {
@@ -56,11 +56,11 @@ __global__ void spmm_kernel(int n, int t, const int* __restrict__ rowptr, const 
     for (int e = e0 + lane; e < e1; e += G) {
       const double2 v = val[e];
       const long long c = col[e];
-      const double2 x0 = X[c * t];
+      const double2 x0 = X[c];
       acc0.x = fma(v.x, x0.x, fma(-v.y, x0.y, acc0.x));
       acc0.y = fma(v.x, x0.y, fma(v.y, x0.x, acc0.y));
       if (t > 1) {
-        const double2 x1 = X[c * t + 1];
+        const double2 x1 = X[n + c];
         acc1.x = fma(v.x, x1.x, fma(-v.y, x1.y, acc1.x));
         acc1.y = fma(v.x, x1.y, fma(v.y, x1.x, acc1.y));
       }
@@ -72,8 +72,8 @@ __global__ void spmm_kernel(int n, int t, const int* __restrict__ rowptr, const 
       acc1.y += __shfl_xor_sync(0xffffffffu, acc1.y, o);
     }
     if (valid && lane == 0) {
-      Y[r * t] = acc0;
-      if (t > 1) Y[r * t + 1] = acc1;
+      Y[r] = acc0;
+      if (t > 1) Y[n + r] = acc1;
     }
   }
 }
@@ -85,8 +85,8 @@ __global__ void colabs_partial_kernel(int n, int t, const double2* __restrict__ 
   double a0 = 0, a1 = 0;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    a0 += cabs(Y[r * t]);
-    if (t > 1) a1 += cabs(Y[r * t + 1]);
+    a0 += cabs(Y[r]);
+    if (t > 1) a1 += cabs(Y[n + r]);
   }
   s0[threadIdx.x] = a0;
   s1[threadIdx.x] = a1;
@@ -129,8 +129,8 @@ __global__ void sign_kernel(long long m, const double2* __restrict__ Y, double2*
 __global__ void rowmax_kernel(int n, int t, const double2* __restrict__ Z, double* __restrict__ h) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    double v = cabs(Z[r * t]);
-    if (t > 1) v = fmax(v, cabs(Z[r * t + 1]));
+    double v = cabs(Z[r]);
+    if (t > 1) v = fmax(v, cabs(Z[n + r]));
     h[r] = v;
   }
 }
@@ -197,18 +197,18 @@ __global__ void init_block_kernel(int n, int t, double2* __restrict__ X) {
   const double inv = 1.0 / n;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    X[r * t] = make_double2(inv, 0.0);
+    X[r] = make_double2(inv, 0.0);
     if (t > 1) {
       const bool neg = (splitmix64(kSeed, (unsigned long long)r) >> 63) != 0;
-      X[r * t + 1] = make_double2(neg ? -inv : inv, 0.0);
+      X[n + r] = make_double2(neg ? -inv : inv, 0.0);
     }
   }
 }
 
-__global__ void set_units_kernel(int t, double2* __restrict__ X, int i0, int i1) {
+__global__ void set_units_kernel(int n, int t, double2* __restrict__ X, int i0, int i1) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    X[(long long)i0 * t] = make_double2(1.0, 0.0);
-    if (t > 1) X[(long long)i1 * t + 1] = make_double2(1.0, 0.0);
+    X[i0] = make_double2(1.0, 0.0);
+    if (t > 1) X[(long long)n + i1] = make_double2(1.0, 0.0);
   }
 }
 
@@ -227,6 +227,26 @@ __global__ void rowabs_max_kernel(int n, const int* __restrict__ rowptr,
   if ((threadIdx.x & 31) == 0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(best));
 }
 
+// ||L||_1 matrix-free: column (i, j) of L holds |(1-omega) H| entries of rows
+// i and j of H, the diagonal D_ij and, when i = j, the rates of the jumps out
+// of i (which sum to dtot_i).
+__global__ void mf_colabs_max_kernel(int Nt, const double* __restrict__ habs,
+                                     const double* __restrict__ ad, const double* __restrict__ hw,
+                                     const double* __restrict__ dtot,
+                                     unsigned long long* __restrict__ out_bits) {
+  const long long n = (long long)Nt * Nt;
+  double best = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(r % Nt), j = (int)(r / Nt);
+    double s = habs[i] + habs[j] + hypot(ad[i] + ad[j], hw[j] - hw[i]);
+    if (i == j) s += dtot[i];
+    best = fmax(best, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(best));
+}
+
 __global__ void roots_kernel(const double* __restrict__ norms, double* __restrict__ dp) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     dp[0] = norms[0];
@@ -238,27 +258,34 @@ __global__ void roots_kernel(const double* __restrict__ norms, double* __restric
 struct Estimator {
   cudaStream_t st;
   int n, t;
-  const Csr* A;
+  const Op* op;
+  const Csr* A;    // CSR operator, or null for matrix-free
   const Csr* AH;
   DevBuf X, Y, W, h, partials, pv, pi, out;
 
   void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
 
-  void mult(const Csr& M, int p, const double2* in, double2* out_, double2* tmp) {
-    // out = M^p in, ping-ponging through tmp
+  void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp) {
+    // out = M^p in (M = L or L^H), ping-ponging through tmp
     const double2* src = in;
     for (int k = 0; k < p; ++k) {
       double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
-      spmm_kernel<<<grid_for((long long)n * 8, 256, 152 * 16), 256, 0, st>>>(
-          n, t, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
+      if (A) {
+        const Csr& M = adjoint ? *AH : *A;
+        QSW_LAUNCH spmm_kernel<<<grid_for((long long)n * 8, 256, 152 * 16), 256, 0, st>>>(
+            n, t, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
+      } else {
+        mf_apply64(*op, adjoint, t, reinterpret_cast<const double*>(src),
+                   reinterpret_cast<double*>(dst), 1.0);
+      }
       src = dst;
     }
     QSW_CUDA_TRY(cudaGetLastError());
   }
 
   void colnorms(const double2* Yp, double* host2) {
-    colabs_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, t, Yp, partials.as<double>());
-    sum_partials_kernel<<<1, 32, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
+    QSW_LAUNCH colabs_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, t, Yp, partials.as<double>());
+    QSW_LAUNCH sum_partials_kernel<<<1, 32, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
     QSW_CUDA_TRY(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
   }
@@ -268,9 +295,9 @@ struct Estimator {
     Excl e{};
     e.n = (int)std::min<size_t>(ex.size(), kMaxExcl);
     for (int q = 0; q < e.n; ++q) e.idx[q] = ex[q];
-    argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, h.as<double>(), e, pv.as<double>(),
+    QSW_LAUNCH argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, h.as<double>(), e, pv.as<double>(),
                                                           pi.as<int>());
-    argmax_final_kernel<<<1, 32, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
+    QSW_LAUNCH argmax_final_kernel<<<1, 32, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
                                           probe, out.as<double>());
     double o[3];
     QSW_CUDA_TRY(cudaMemcpyAsync(o, out.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -284,14 +311,14 @@ struct Estimator {
     double2* Xp = X.as<double2>();
     double2* Yp = Y.as<double2>();
     double2* Wp = W.as<double2>();
-    init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Xp);
+    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Xp);
     QSW_CUDA_TRY(cudaGetLastError());
     std::vector<int> hist;
     double est_old = 0.0, est = 0.0;
     int ind[2] = {0, 0};
     int ind_best = 0;
     for (int k = 1;; ++k) {
-      mult(*A, p, Xp, Yp, Wp);
+      mult(false, p, Xp, Yp, Wp);
       double cn[2] = {0, 0};
       colnorms(Yp, cn);
       const int jbest = (t > 1 && cn[1] > cn[0]) ? 1 : 0;
@@ -303,9 +330,9 @@ struct Estimator {
       }
       est_old = est;
       if (k > kItMax) break;
-      sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>((long long)n * t, Yp, Xp);
-      mult(*AH, p, Xp, Yp, Wp);   // Z = (A^H)^p S, in Y
-      rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
+      QSW_LAUNCH sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>((long long)n * t, Yp, Xp);
+      mult(true, p, Xp, Yp, Wp);   // Z = (A^H)^p S, in Y
+      QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
       QSW_CUDA_TRY(cudaGetLastError());
       double hmax, hbest;
       int imax;
@@ -331,7 +358,7 @@ struct Estimator {
       ind[0] = fresh[0];
       ind[1] = fresh[1];
       QSW_CUDA_TRY(cudaMemsetAsync(Xp, 0, sizeof(double2) * (size_t)n * t, st));
-      set_units_kernel<<<1, 32, 0, st>>>(t, Xp, ind[0], ind[1] < 0 ? 0 : ind[1]);
+      QSW_LAUNCH set_units_kernel<<<1, 32, 0, st>>>(n, t, Xp, ind[0], ind[1] < 0 ? 0 : ind[1]);
       QSW_CUDA_TRY(cudaGetLastError());
       hist.push_back(ind[0]);
       if (t > 1) hist.push_back(ind[1]);
@@ -342,16 +369,21 @@ struct Estimator {
 
 }  // namespace
 
-void compute_norms(Op& op, const Csr& L, const Csr& LH) {
+void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   cudaStream_t st = op.ctx->stream;
   const int n = (int)op.n;
   // exact ||L||_1
   DevBuf bits;
   bits.alloc(sizeof(unsigned long long));
   QSW_CUDA_TRY(cudaMemsetAsync(bits.p, 0, sizeof(unsigned long long), st));
-  rowabs_max_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(n, LH.rowptr.as<int>(),
-                                                                 LH.val.as<double2>(),
-                                                                 bits.as<unsigned long long>());
+  if (LH) {
+    QSW_LAUNCH rowabs_max_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(
+        n, LH->rowptr.as<int>(), LH->val.as<double2>(), bits.as<unsigned long long>());
+  } else {
+    QSW_LAUNCH mf_colabs_max_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(
+        op.Nt, op.mf.habs.as<double>(), op.mf.ad64.as<double>(), op.mf.hw64.as<double>(),
+        op.g.dtot.as<double>(), bits.as<unsigned long long>());
+  }
   QSW_CUDA_TRY(cudaGetLastError());
   unsigned long long b = 0;
   QSW_CUDA_TRY(cudaMemcpyAsync(&b, bits.p, sizeof(b), cudaMemcpyDeviceToHost, st));
@@ -364,8 +396,9 @@ void compute_norms(Op& op, const Csr& L, const Csr& LH) {
   E.st = st;
   E.n = n;
   E.t = n >= 2 ? kEll : 1;
-  E.A = &L;
-  E.AH = &LH;
+  E.op = &op;
+  E.A = L;
+  E.AH = LH;
   E.X.alloc(sizeof(double2) * (size_t)n * E.t);
   E.Y.alloc(sizeof(double2) * (size_t)n * E.t);
   E.W.alloc(sizeof(double2) * (size_t)n * E.t);
@@ -382,7 +415,7 @@ void compute_norms(Op& op, const Csr& L, const Csr& LH) {
   QSW_CUDA_TRY(cudaMemcpyAsync(nd.p, op.norms, sizeof(double) * kNormPowers,
                                cudaMemcpyHostToDevice, st));
   op.dp_dev.alloc(sizeof(double) * (kNormPowers + 1));
-  roots_kernel<<<1, 32, 0, st>>>(nd.as<double>(), op.dp_dev.as<double>());
+  QSW_LAUNCH roots_kernel<<<1, 32, 0, st>>>(nd.as<double>(), op.dp_dev.as<double>());
   QSW_CUDA_TRY(cudaGetLastError());
   QSW_CUDA_TRY(cudaMemcpyAsync(op.dp, op.dp_dev.p, sizeof(double) * (kNormPowers + 1),
                                cudaMemcpyDeviceToHost, st));

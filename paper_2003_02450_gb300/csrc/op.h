@@ -28,6 +28,7 @@ struct GraphDev {
   DevBuf j_rowptr, j_col, j_val;     // rows = destination i (for L)
   DevBuf jt_rowptr, jt_col, jt_val;  // rows = source q (for L^H)
   DevBuf dtot;                       // [Nt] total jump rate leaving each vertex
+  int n_jumps = 0;                   // entries of J (= entries of J^T)
   DevBuf scratch;                    // small integer scratch
 };
 
@@ -37,9 +38,20 @@ struct Csr {
   bool fp32 = false;
 };
 
+// Coefficients of the matrix-free operator (matfree.cuh), FP64 and FP32 copies.
+struct MfData {
+  DevBuf hval64, hval32;   // (1 - omega) H_offdiag
+  DevBuf ad64, ad32;       // -dtot / 2
+  DevBuf hw64, hw32;       // (1 - omega) H_vv
+  DevBuf jval32, jtval32;  // jump rates (FP64 copies live in GraphDev)
+  DevBuf habs;             // [Nt] sum_m |(1 - omega) H_vm|, for the exact 1-norm
+};
+
 struct Op {
   qsw_ctx* ctx = nullptr;
   int precision = QSW_C128;
+  int opkind = QSW_OPERATOR_MATRIX_FREE;
+  long long nnz_csr = 0;   // entries of the CSR form (closed form)
   double omega = 0.0;
   int N = 0, Nt = 0;
   int64_t n = 0;
@@ -53,14 +65,15 @@ struct Op {
   std::vector<double> src_r, snk_r;
 
   GraphDev g;
-  Csr L;           // the superoperator
+  MfData mf;
+  Csr L;           // the superoperator in CSR (assembled for QSW_OPERATOR_CSR or on export)
   double norms[kNormPowers] = {0};   // ||L||_1, est ||L^p||_1
   double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
   DevBuf dp_dev;
   int tpr = 8;     // SpMV threads per row
 
   // series workspace
-  DevBuf kbuf, ring, jobs, ctrl;
+  DevBuf kbuf, ring, jobs, ctrl, scratch;
 };
 
 // graph.cu
@@ -69,8 +82,9 @@ void build_jumps(Op& op);           // J, J^T, dtot for op.omega
 // assemble.cu
 void assemble(Op& op, bool adjoint, Csr& out);   // L (adjoint = false) or L^H, FP64 values
 void to_fp32(Op& op, Csr& m);                    // replace FP64 values by FP32
+void prep_matfree(Op& op);         // MfData for op.omega
 // norms.cu
-void compute_norms(Op& op, const Csr& L, const Csr& LH);
+void compute_norms(Op& op, const Csr* L, const Csr* LH);   // null: matrix-free
 // series.cu
 void upload_theta(int device);
 void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
@@ -79,6 +93,10 @@ void apply(const Op& op, const double* d_x, double* d_y);
 void populations(const Op& op, const double* d_rho, int count, double* d_pops);
 void initial_state_from_pops(const Op& op, const double* d_pops, double* d_state);
 void widen_values(const Op& op, double* d_val);
+double op_bytes(const Op& op);
+template <class R> struct MfOp;
+template <class R> MfOp<R> make_mf(const Op& op, bool adjoint);
+void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
 int choose_tpr(double avg_row);
 
 inline unsigned grid_for(int64_t items, int block, int max_blocks = 1 << 20) {

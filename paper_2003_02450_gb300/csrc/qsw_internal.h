@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,10 @@ constexpr int kPMax = 8;      // p_max (largest p with p(p-1) <= m_max + 1)
 constexpr int kEll = 2;       // columns of the 1-norm estimator
 constexpr int kNormPowers = 9;  // ||L^p||_1, p = 1..9 (paper Section 4 footnote)
 constexpr int kMaxPorts = 4096;
+
+// Number of kernels this library has launched in this process (all devices).
+extern std::atomic<long long> g_launches;
+#define QSW_LAUNCH ::qsw::g_launches.fetch_add(1, std::memory_order_relaxed),
 
 // ------------------------------------------------------------------ errors
 struct Error {

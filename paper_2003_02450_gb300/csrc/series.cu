@@ -2,33 +2,35 @@
 // Al-Mohy & Higham as used by the paper (Section 3.1), run as ONE persistent
 // cooperative kernel per call.
 //
-// The host-independent plan (params.cuh) turns the call into a list of Taylor
-// blocks.  A block with input Z, span hspan = d h and outputs k = 1..d computes
+// The plan (params.cuh, built on the device by plan_kernel) turns the call into
+// a list of Taylor blocks.  A block with input Z, span hspan = d h and outputs
+// k = 1..d computes
 //     Khat_0 = Z,   Khat_p = (hspan / p) L Khat_{p-1},
 //     F_k = Z + sum_{p=1}^{p_k} (k/d)^p Khat_p,
 // which is Algorithm 5.2's  F_k = sum_p k^p K_p  with K_p = (hA)^p Z / p!
 // (Khat_p = d^p K_p), and with d = 1 one stage of Algorithm 3.2.  Output k stops
 // after the first p with  c1 + c2 <= tol ||F_k||_inf,  c2 = (k/d)^p ||Khat_p||_inf,
 // c1 the previous term's norm (||Z||_inf at p = 1).  The powers are formed once
-// per block and every active output is updated in the same pass, so the block
-// costs max_k p_k applications of L~, as in the paper's `series` (Section 5:
-// one time series for about the cost of one `step`).
+// per block and every active output is updated in the same pass, so a block
+// costs max_k p_k applications of L~ (paper Section 5: a whole time series for
+// about the cost of one `step`).
 //
-// One term = one pass over the rows: the complex SpMV (TPR lanes per row,
-// coalesced column/value streams, vector gathers through L2), the scaled store
-// of Khat_p, the FP64 update of every active F_k, and the inf-norm partial
-// maxima (warp shuffles, then one atomicMax per block).  A grid barrier with a
-// bounded wait separates terms; after it every block reads the same maxima and
-// takes the same stop decisions, so no host round trip is needed.
+// One term = one pass over the n elements: apply L~ (matrix-free, or CSR), scale,
+// store Khat_p, update every active F_k in FP64, and keep running inf-norm
+// maxima (squared moduli compared as integer bit patterns, which keeps them
+// off the FP64 pipe).  A grid barrier with a bounded wait separates terms;
+// after it every block reads the same maxima and takes the same stop decisions,
+// so the host is never consulted inside the series.
 //
-// Precision: VT = double2 (complex128) or float2 (complex64 bulk: FP32 matrix
-// values, FP32 Taylor terms and FP32 accumulation of each product).  The F_k
-// accumulators, the norms and the stop test are FP64 in both cases.
-#include <cooperative_groups.h>
+// Precision: VT = double2 (complex128) or float2 (complex64 bulk: FP32 operator
+// coefficients, FP32 Taylor terms, FP32 accumulation of every product).  The
+// F_k accumulators, the norms and the stop test are FP64 in both cases.
 #include <math.h>
+#include <string.h>
 
 #include <algorithm>
 
+#include "matfree.cuh"
 #include "op.h"
 #include "params.cuh"
 
@@ -40,11 +42,14 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kKpl = 4;                 // outputs owned per lane
-constexpr int kDMax = kKpl * 32;        // max outputs per job at TPR = 32
+constexpr int kDMax = 128;              // outputs per Taylor block
+constexpr int kKReg = 4;                // outputs whose running max lives in registers
+constexpr int kRpt = 2;                 // rows per thread in one matrix-free pass
 constexpr unsigned kSpinLimit = 1u << 24;  // bounded barrier wait (~seconds)
 
 enum : int { kErrNone = 0, kErrBarrier = 1, kErrPlan = 2 };
+enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2 };
+static_assert(kItemRows == 32 * kRpt, "a work item is one row per lane per kRpt");
 
 struct Ctrl {
   unsigned int bar_count;
@@ -52,19 +57,25 @@ struct Ctrl {
   int error;
   int njobs;
   unsigned long long matvecs;
+  unsigned long long fupdates;   // sum over terms of the outputs updated
+  unsigned int work[3];          // matrix-free column counters, one per term slot
+  unsigned int pad;
   unsigned long long gmax[3][1 + kDMax];
 };
 
 struct SeriesArgs {
   int n, nt;
-  const int* rowptr;
+  const int* rowptr;     // CSR operator
   const int* col;
   const void* val;
+  MfOp<double> mf64;     // matrix-free operator (one of the two is used)
+  MfOp<float> mf32;
   void* k0;
   void* k1;
   const double2* rho0;
   double2* slots;
   int ring;              // 0: series index k -> slot k; else k % ring
+  int mirror;            // Hermitian form with caller outputs: fill lower triangles
   double* pops;          // (steps+1) x nt or null
   const Job* jobs;
   int njobs;
@@ -76,14 +87,13 @@ template <class VT> struct Cplx;
 template <> struct Cplx<double2> {
   using R = double;
   __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+  __device__ static const MfOp<double>& mf(const SeriesArgs& a) { return a.mf64; }
 };
 template <> struct Cplx<float2> {
   using R = float;
   __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+  __device__ static const MfOp<float>& mf(const SeriesArgs& a) { return a.mf32; }
 };
-
-__device__ __forceinline__ double2 ld_cg(const double2* p) { return __ldcg(p); }
-__device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
 
 __device__ __forceinline__ double2* slot_ptr(const SeriesArgs& a, int idx) {
   const long long s = a.ring ? (idx % a.ring) : idx;
@@ -95,6 +105,13 @@ __device__ __forceinline__ unsigned long long as_bits(double v) {
 }
 __device__ __forceinline__ double from_bits(unsigned long long b) {
   return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ unsigned long long umax64(unsigned long long a, unsigned long long b) {
+  return a > b ? a : b;
+}
+__device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
+  for (int o = 16; o > 0; o >>= 1) v = umax64(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
 }
 
 // Grid barrier for a cooperative launch (all blocks co-resident).  The wait is
@@ -131,31 +148,67 @@ __device__ bool grid_barrier(Ctrl* c) {
   return s_ok != 0;
 }
 
-template <class VT, int TPR>
-__global__ void __launch_bounds__(kBlock)
+// Per-thread epilogue state of one Taylor term.
+template <class VT> struct Epilogue {
+  using R = typename Cplx<VT>::R;
+  const SeriesArgs* a;
+  VT* knext;
+  int out0, d;
+  double coef[kKReg];
+  bool own[kKReg];
+  unsigned long long kmax;
+  unsigned long long fmax[kKReg];
+  const double* s_coef;
+  const int* s_active;
+  unsigned long long* s_fmax_extra;   // outputs k >= kKReg (shared, block-level)
+
+  __device__ void consume(long long r, R yx, R yy) {
+    knext[r] = Cplx<VT>::make(yx, yy);
+    const double dx = (double)yx, dy = (double)yy;
+    kmax = umax64(kmax, as_bits(dx * dx + dy * dy));
+#pragma unroll
+    for (int u = 0; u < kKReg; ++u) {
+      if (own[u]) {
+        double2* F = slot_ptr(*a, out0 + u) + r;
+        double2 f = __ldcg(F);
+        f.x = fma(coef[u], dx, f.x);
+        f.y = fma(coef[u], dy, f.y);
+        *F = f;
+        fmax[u] = umax64(fmax[u], as_bits(f.x * f.x + f.y * f.y));
+      }
+    }
+    for (int k = kKReg; k < d; ++k) {
+      if (!s_active[k]) continue;
+      double2* F = slot_ptr(*a, out0 + k) + r;
+      double2 f = __ldcg(F);
+      f.x = fma(s_coef[k], dx, f.x);
+      f.y = fma(s_coef[k], dy, f.y);
+      *F = f;
+      atomicMax(&s_fmax_extra[k], as_bits(f.x * f.x + f.y * f.y));
+    }
+  }
+};
+
+template <class VT, int OPK, int TPR>
+__global__ void __launch_bounds__(kBlock, 3)
 series_kernel(SeriesArgs a) {
   using R = typename Cplx<VT>::R;
-  __shared__ double s_red[kWarps][1 + kDMax];
+  __shared__ unsigned long long s_red[kWarps][1 + kKReg];
+  __shared__ unsigned long long s_fmax_extra[kDMax];
   __shared__ double s_c1[kDMax];
   __shared__ double s_coef[kDMax];
   __shared__ double s_step[kDMax];
   __shared__ int s_active[kDMax];
   __shared__ int s_any;
+  __shared__ int s_item;
   __shared__ double s_normk;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  const int glane = lane % TPR;
-  constexpr int kGpw = 32 / TPR;   // row groups per warp
-  const long long wglobal = ((long long)blockIdx.x * kBlock + tid) / 32;
-  const long long rstride = (long long)gridDim.x * kWarps * kGpw;
   const long long gthread = (long long)blockIdx.x * kBlock + tid;
   const long long nthreads = (long long)gridDim.x * kBlock;
   Ctrl* ctrl = a.ctrl;
-  const VT* __restrict__ val = static_cast<const VT*>(a.val);
-  const int* __restrict__ col = a.col;
-  const int* __restrict__ rowptr = a.rowptr;
   unsigned term = 0;
 
   for (int jb = 0; jb < a.njobs; ++jb) {
@@ -165,25 +218,26 @@ series_kernel(SeriesArgs a) {
     VT* knext = static_cast<VT*>(a.k1);
 
     // ---- init: Khat_0 = Z, F_k = Z, ||Z||_inf
-    double zmax = 0.0;
+    unsigned long long zmax = 0;
     for (long long r = gthread; r < a.n; r += nthreads) {
-      const double2 z = ld_cg(Z + r);
+      const double2 z = __ldcg(Z + r);
       kcur[r] = Cplx<VT>::make((R)z.x, (R)z.y);
       for (int k = 0; k < J.d; ++k) slot_ptr(a, J.out_index0 + k)[r] = z;
-      zmax = fmax(zmax, z.x * z.x + z.y * z.y);
+      zmax = umax64(zmax, as_bits(z.x * z.x + z.y * z.y));
     }
-    for (int o = 16; o > 0; o >>= 1) zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+    zmax = warp_umax(zmax);
     if (lane == 0) s_red[warp][0] = zmax;
     __syncthreads();
     unsigned slot3 = term % 3;
     if (tid == 0) {
-      double m = 0.0;
-      for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w][0]);
-      atomicMax(&ctrl->gmax[slot3][0], as_bits(m));
+      unsigned long long m = 0;
+      for (int w = 0; w < kWarps; ++w) m = umax64(m, s_red[w][0]);
+      atomicMax(&ctrl->gmax[slot3][0], m);
     }
     if (blockIdx.x == 0) {
       const unsigned nx = (term + 1) % 3;
       for (int q = tid; q <= J.d; q += kBlock) ctrl->gmax[nx][q] = 0ULL;
+      if (tid == 0) ctrl->work[nx] = 0u;
     }
     if (!grid_barrier(ctrl)) return;
     const double normz = sqrt(from_bits(__ldcg(&ctrl->gmax[slot3][0])));
@@ -199,96 +253,131 @@ series_kernel(SeriesArgs a) {
     for (int p = 1; p <= J.m; ++p) {
       const double scale = J.hspan / p;
       const R rscale = (R)scale;
-      for (int k = tid; k < J.d; k += kBlock) s_coef[k] *= s_step[k];
-      __syncthreads();
-      double coef[kKpl];
-      int own[kKpl];
-#pragma unroll
-      for (int u = 0; u < kKpl; ++u) {
-        const int k = glane + u * TPR;
-        own[u] = (k < J.d) ? s_active[k] : 0;
-        coef[u] = own[u] ? s_coef[k] : 0.0;
+      slot3 = term % 3;
+      for (int k = tid; k < J.d; k += kBlock) {
+        s_coef[k] *= s_step[k];
+        s_fmax_extra[k] = 0ULL;
       }
-      double kmax = 0.0;
-      double fmaxv[kKpl];
+      __syncthreads();
+      Epilogue<VT> ep;
+      ep.a = &a;
+      ep.knext = knext;
+      ep.out0 = J.out_index0;
+      ep.d = J.d;
+      ep.s_coef = s_coef;
+      ep.s_active = s_active;
+      ep.s_fmax_extra = s_fmax_extra;
+      ep.kmax = 0;
 #pragma unroll
-      for (int u = 0; u < kKpl; ++u) fmaxv[u] = 0.0;
+      for (int u = 0; u < kKReg; ++u) {
+        ep.own[u] = u < J.d && s_active[u];
+        ep.coef[u] = ep.own[u] ? s_coef[u] : 0.0;
+        ep.fmax[u] = 0;
+      }
 
-      // warp-uniform row loop: every lane takes part in the group shuffles
-      for (long long rb = wglobal * kGpw; rb < a.n; rb += rstride) {
-        const long long r = rb + lane / TPR;
-        const bool valid = r < a.n;
-        const int e0 = valid ? rowptr[r] : 0;
-        const int e1 = valid ? rowptr[r + 1] : 0;
-        R ax = 0, ay = 0;
-        int e = e0 + glane;
-        for (; e + TPR < e1; e += 2 * TPR) {
-          const int c0 = __ldcs(col + e);
-          const int c1 = __ldcs(col + e + TPR);
-          const VT v0 = __ldcs(val + e);
-          const VT v1 = __ldcs(val + e + TPR);
-          const VT x0 = ld_cg(kcur + c0);
-          const VT x1 = ld_cg(kcur + c1);
-          ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
-          ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
-          ax = fma(v1.x, x1.x, fma(-v1.y, x1.y, ax));
-          ay = fma(v1.x, x1.y, fma(v1.y, x1.x, ay));
-        }
-        if (e < e1) {
-          const int c0 = __ldcs(col + e);
-          const VT v0 = __ldcs(val + e);
-          const VT x0 = ld_cg(kcur + c0);
-          ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
-          ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
-        }
+      if (OPK != kOpCsr) {
+        // ---- matrix-free sweep: warps take 64-row chunks of columns from a
+        // counter (no block-level synchronisation inside the pass)
+        constexpr bool kHerm = OPK == kOpMatfreeHerm;
+        const MfOp<R>& op = Cplx<VT>::mf(a);
+        const int nt = a.nt;
+        const long long nitems = mf_item_count(nt, kHerm);
+        for (;;) {
+          unsigned int k = 0;
+          if (lane == 0) k = atomicAdd(&ctrl->work[slot3], 1u);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if ((long long)k >= nitems) break;
+          int j, i0;
+          mf_item(k, nt, kHerm, j, i0);
+          int irow[kRpt];
 #pragma unroll
-        for (int o = TPR / 2; o > 0; o >>= 1) {
-          ax += __shfl_xor_sync(0xffffffffu, ax, o, TPR);
-          ay += __shfl_xor_sync(0xffffffffu, ay, o, TPR);
-        }
-        if (!valid) continue;
-        const R yx = ax * rscale, yy = ay * rscale;
-        if (glane == 0) knext[r] = Cplx<VT>::make(yx, yy);
-        const double dyx = (double)yx, dyy = (double)yy;
-        kmax = fmax(kmax, dyx * dyx + dyy * dyy);
+          for (int u = 0; u < kRpt; ++u) {
+            const int i = i0 + lane + 32 * u;
+            irow[u] = (i < nt && (!kHerm || i <= j)) ? i : -1;
+          }
+          R bx[kRpt], by[kRpt];
+          mf_partB<R, VT, kRpt, kHerm>(op, kcur, j, irow, bx, by);
 #pragma unroll
-        for (int u = 0; u < kKpl; ++u) {
-          if (own[u]) {
-            double2* F = slot_ptr(a, J.out_index0 + glane + u * TPR) + r;
-            double2 f = ld_cg(F);
-            f.x = fma(coef[u], dyx, f.x);
-            f.y = fma(coef[u], dyy, f.y);
-            *F = f;
-            fmaxv[u] = fmax(fmaxv[u], f.x * f.x + f.y * f.y);
+          for (int u = 0; u < kRpt; ++u) {
+            if (irow[u] < 0) continue;
+            R yx, yy;
+            mf_finish<R, VT, false, kHerm>(op, kcur, irow[u], j, bx[u], by[u], yx, yy);
+            ep.consume(irow[u] + (long long)nt * j, yx * rscale, yy * rscale);
           }
         }
-      }
-      // ---- block reduction of ||Khat_p||^2 and ||F_k||^2 partial maxima
-      for (int o = 16; o > 0; o >>= 1) kmax = fmax(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+      } else {
+        // ---- CSR sweep: TPR lanes per row, warp-uniform row loop
+        const VT* __restrict__ val = static_cast<const VT*>(a.val);
+        const int* __restrict__ col = a.col;
+        const int* __restrict__ rowptr = a.rowptr;
+        const int glane = lane % TPR;
+        constexpr int kGpw = 32 / TPR;
+        const long long wglobal = gthread / 32;
+        const long long rstride = (long long)gridDim.x * kWarps * kGpw;
+        for (long long rb = wglobal * kGpw; rb < a.n; rb += rstride) {
+          const long long r = rb + lane / TPR;
+          const bool valid = r < a.n;
+          const int e0 = valid ? rowptr[r] : 0;
+          const int e1 = valid ? rowptr[r + 1] : 0;
+          R ax = 0, ay = 0;
+          int e = e0 + glane;
+          for (; e + TPR < e1; e += 2 * TPR) {
+            const int c0 = __ldcs(col + e);
+            const int c1 = __ldcs(col + e + TPR);
+            const VT v0 = __ldcs(val + e);
+            const VT v1 = __ldcs(val + e + TPR);
+            const VT x0 = __ldcg(kcur + c0);
+            const VT x1 = __ldcg(kcur + c1);
+            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+            ax = fma(v1.x, x1.x, fma(-v1.y, x1.y, ax));
+            ay = fma(v1.x, x1.y, fma(v1.y, x1.x, ay));
+          }
+          if (e < e1) {
+            const int c0 = __ldcs(col + e);
+            const VT v0 = __ldcs(val + e);
+            const VT x0 = __ldcg(kcur + c0);
+            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+          }
 #pragma unroll
-      for (int u = 0; u < kKpl; ++u)
-        for (int o = TPR; o < 32; o <<= 1)
-          fmaxv[u] = fmax(fmaxv[u], __shfl_xor_sync(0xffffffffu, fmaxv[u], o));
-      if (lane == 0) s_red[warp][0] = kmax;
-      if (lane < TPR) {
-#pragma unroll
-        for (int u = 0; u < kKpl; ++u) {
-          const int k = lane + u * TPR;
-          if (k < J.d) s_red[warp][1 + k] = fmaxv[u];
+          for (int o = TPR / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o, TPR);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o, TPR);
+          }
+          if (valid && glane == 0) ep.consume(r, ax * rscale, ay * rscale);
         }
       }
+
+      // ---- block reduction of the squared-norm maxima, one atomic per value
+      unsigned long long km = warp_umax(ep.kmax);
+      if (lane == 0) s_red[warp][0] = km;
+#pragma unroll
+      for (int u = 0; u < kKReg; ++u) {
+        const unsigned long long fm = warp_umax(ep.fmax[u]);
+        if (lane == 0) s_red[warp][1 + u] = fm;
+      }
       __syncthreads();
-      slot3 = term % 3;
       for (int q = tid; q <= J.d; q += kBlock) {
         if (q > 0 && !s_active[q - 1]) continue;
-        double m = 0.0;
-        for (int w = 0; w < kWarps; ++w) m = fmax(m, s_red[w][q]);
-        atomicMax(&ctrl->gmax[slot3][q], as_bits(m));
+        unsigned long long m = 0;
+        if (q <= kKReg) {
+          for (int w = 0; w < kWarps; ++w) m = umax64(m, s_red[w][q]);
+        } else {
+          m = s_fmax_extra[q - 1];
+        }
+        atomicMax(&ctrl->gmax[slot3][q], m);
       }
       if (blockIdx.x == 0) {
         const unsigned nx = (term + 1) % 3;
         for (int q = tid; q <= J.d; q += kBlock) ctrl->gmax[nx][q] = 0ULL;
-        if (tid == 0) atomicAdd(&ctrl->matvecs, 1ULL);
+        if (tid == 0) {
+          ctrl->work[nx] = 0u;
+          int act = 0;
+          for (int k = 0; k < J.d; ++k) act += s_active[k];
+          atomicAdd(&ctrl->matvecs, 1ULL);
+          atomicAdd(&ctrl->fupdates, (unsigned long long)act);
+        }
       }
       if (!grid_barrier(ctrl)) return;
       ++term;
@@ -313,13 +402,27 @@ series_kernel(SeriesArgs a) {
       if (!s_any) break;
     }
 
+    // ---- Hermitian form: complete the caller's outputs from their upper triangles
+    if (OPK == kOpMatfreeHerm && a.mirror && J.final_outputs) {
+      const long long tot = (long long)J.d * a.n;
+      for (long long q = gthread; q < tot; q += nthreads) {
+        const int k = (int)(q / a.n);
+        const long long r = q % a.n;
+        const int i = (int)(r % a.nt), j = (int)(r / a.nt);
+        if (i <= j) continue;
+        double2* F = slot_ptr(a, J.out_index0 + k);
+        double2 z = __ldcg(F + j + (long long)a.nt * i);
+        F[r] = make_double2(z.x, -z.y);
+      }
+    }
+
     // ---- populations of the finished outputs
     if (J.final_outputs && a.pops) {
       const long long tot = (long long)J.d * a.nt;
       for (long long q = gthread; q < tot; q += nthreads) {
         const int k = (int)(q / a.nt);
         const int v = (int)(q % a.nt);
-        const double2 z = ld_cg(slot_ptr(a, J.out_index0 + k) + (long long)v * (a.nt + 1));
+        const double2 z = __ldcg(slot_ptr(a, J.out_index0 + k) + (long long)v * (a.nt + 1));
         a.pops[(long long)(J.out_index0 + k) * a.nt + v] = z.x;
       }
       if (a.ring) {
@@ -339,10 +442,42 @@ __global__ void plan_kernel(const double* __restrict__ dp, int prec, double t0, 
   }
 }
 
+// y = scale L x (or scale L^H x) for `cols` vectors stored one after another
+// (n apart), matrix-free.  Blocks stride over the columns j of the density
+// matrix.
+template <class R, class VT, bool ADJ>
+__global__ void __launch_bounds__(kBlock)
+mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__ y, double scale) {
+  const long long n = (long long)op.Nt * op.Nt;
+  for (int j = blockIdx.x; j < op.Nt; j += gridDim.x) {
+    for (int i0 = 0; i0 < op.Nt; i0 += kBlock * kRpt) {
+      int irow[kRpt];
+#pragma unroll
+      for (int u = 0; u < kRpt; ++u) {
+        const int i = i0 + threadIdx.x + u * kBlock;
+        irow[u] = i < op.Nt ? i : -1;
+      }
+      for (int c = 0; c < cols; ++c) {
+        const VT* xc = x + c * n;
+        R bx[kRpt], by[kRpt];
+        mf_partB<R, VT, kRpt, false>(op, xc, j, irow, bx, by);
+#pragma unroll
+        for (int u = 0; u < kRpt; ++u) {
+          if (irow[u] < 0) continue;
+          R yx, yy;
+          mf_finish<R, VT, ADJ, false>(op, xc, irow[u], j, bx[u], by[u], yx, yy);
+          y[c * n + irow[u] + (long long)op.Nt * j] =
+              Cplx<VT>::make(yx * (R)scale, yy * (R)scale);
+        }
+      }
+    }
+  }
+}
+
 template <class VT>
-__global__ void apply_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
-                             const VT* __restrict__ val, const double2* __restrict__ x,
-                             double2* __restrict__ y) {
+__global__ void apply_csr_kernel(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
+                                 const VT* __restrict__ val, const double2* __restrict__ x,
+                                 double2* __restrict__ y) {
   using R = typename Cplx<VT>::R;
   constexpr int G = 8;
   const int lane = threadIdx.x % G;
@@ -368,6 +503,40 @@ __global__ void apply_kernel(int n, const int* __restrict__ rowptr, const int* _
   }
 }
 
+// max |x_ij - conj(x_ji)|^2 and max |x_ij|^2 as bit patterns (one atomic per warp)
+__global__ void herm_check_kernel(int nt, const double2* __restrict__ x,
+                                  unsigned long long* __restrict__ out) {
+  const long long n = (long long)nt * nt;
+  unsigned long long da = 0, xa = 0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(r % nt), j = (int)(r / nt);
+    const double2 u = x[r];
+    const double2 v = x[j + (long long)nt * i];
+    const double ex = u.x - v.x, ey = u.y + v.y;
+    da = umax64(da, as_bits(ex * ex + ey * ey));
+    xa = umax64(xa, as_bits(u.x * u.x + u.y * u.y));
+  }
+  da = warp_umax(da);
+  xa = warp_umax(xa);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], da);
+    atomicMax(&out[1], xa);
+  }
+}
+
+__global__ void narrow_vec_kernel(long long n, const double2* __restrict__ in, float2* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+
+__global__ void widen_vec_kernel(long long n, const float2* __restrict__ in, double2* __restrict__ out) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    out[e] = make_double2((double)in[e].x, (double)in[e].y);
+}
+
 __global__ void pops_kernel(int count, int nt, long long n, const double2* __restrict__ rho,
                             double* __restrict__ pops) {
   const long long tot = (long long)count * nt;
@@ -376,14 +545,6 @@ __global__ void pops_kernel(int count, int nt, long long n, const double2* __res
     const long long c = q / nt;
     const long long v = q % nt;
     pops[q] = rho[c * n + v * (nt + 1)].x;
-  }
-}
-
-__global__ void widen_kernel(long long nnz, const float2* __restrict__ in, double2* __restrict__ out) {
-  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nnz;
-       e += (long long)gridDim.x * blockDim.x) {
-    const float2 v = in[e];
-    out[e] = make_double2((double)v.x, (double)v.y);
   }
 }
 
@@ -396,30 +557,36 @@ __global__ void diag_state_kernel(int nt, long long n, const double* __restrict_
   }
 }
 
-template <class VT, int TPR>
+template <class VT, int OPK, int TPR>
 cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* grid_out) {
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, series_kernel<VT, TPR>,
-                                                                kBlock, 0);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &per_sm, series_kernel<VT, OPK, TPR>, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  long long want = ((long long)a.n * TPR + kBlock - 1) / kBlock;
-  long long maxg = (long long)per_sm * sms;
-  int grid = (int)std::max<long long>(1, std::min(want, maxg));
+  const long long want = OPK != kOpCsr ? (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps
+                                       : ((long long)a.n * TPR + kBlock - 1) / kBlock;
+  const long long maxg = (long long)per_sm * sms;
+  const int grid = (int)std::max<long long>(1, std::min(want, maxg));
   *grid_out = grid;
   SeriesArgs args = a;
   void* params[] = {&args};
-  return cudaLaunchCooperativeKernel((const void*)series_kernel<VT, TPR>, dim3(grid), dim3(kBlock),
-                                     params, 0, st);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaLaunchCooperativeKernel((const void*)series_kernel<VT, OPK, TPR>, dim3(grid),
+                                     dim3(kBlock), params, 0, st);
 }
 
 template <class VT>
-cudaError_t launch_series_tpr(int tpr, const SeriesArgs& a, int sms, cudaStream_t st, int* g) {
+cudaError_t launch_series_op(const Op& op, int tpr, bool herm, const SeriesArgs& a, int sms,
+                             cudaStream_t st, int* g) {
+  if (op.opkind == QSW_OPERATOR_MATRIX_FREE)
+    return herm ? launch_series<VT, kOpMatfreeHerm, 1>(a, sms, st, g)
+                : launch_series<VT, kOpMatfree, 1>(a, sms, st, g);
   switch (tpr) {
-    case 4: return launch_series<VT, 4>(a, sms, st, g);
-    case 8: return launch_series<VT, 8>(a, sms, st, g);
-    case 16: return launch_series<VT, 16>(a, sms, st, g);
-    default: return launch_series<VT, 32>(a, sms, st, g);
+    case 4: return launch_series<VT, kOpCsr, 4>(a, sms, st, g);
+    case 8: return launch_series<VT, kOpCsr, 8>(a, sms, st, g);
+    case 16: return launch_series<VT, kOpCsr, 16>(a, sms, st, g);
+    default: return launch_series<VT, kOpCsr, 32>(a, sms, st, g);
   }
 }
 
@@ -439,6 +606,48 @@ void upload_theta(int device) {
                                   sizeof(double) * kMMax));
 }
 
+template <class R> MfOp<R> make_mf(const Op& op, bool adjoint) {
+  const MfData& m = op.mf;
+  const bool f = sizeof(R) == sizeof(float);
+  MfOp<R> o;
+  o.N = op.omega < 1.0 ? op.N : 0;   // the commutator vanishes at omega = 1
+  o.Nt = op.Nt;
+  o.hrow = op.g.hoff_rowptr.as<int>();
+  o.hcol = op.g.hoff_col.as<int>();
+  o.hval = static_cast<const R*>(f ? m.hval32.p : m.hval64.p);
+  o.ad = static_cast<const R*>(f ? m.ad32.p : m.ad64.p);
+  o.hw = static_cast<const R*>(f ? m.hw32.p : m.hw64.p);
+  o.jrow = adjoint ? op.g.jt_rowptr.as<int>() : op.g.j_rowptr.as<int>();
+  o.jcol = adjoint ? op.g.jt_col.as<int>() : op.g.j_col.as<int>();
+  o.jval = static_cast<const R*>(adjoint ? (f ? m.jtval32.p : op.g.jt_val.p)
+                                         : (f ? m.jval32.p : op.g.j_val.p));
+  return o;
+}
+template MfOp<double> make_mf<double>(const Op&, bool);
+template MfOp<float> make_mf<float>(const Op&, bool);
+
+void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale) {
+  const MfOp<double> m = make_mf<double>(op, adjoint);
+  const unsigned grid = (unsigned)std::min(op.Nt, 152 * 8);
+  if (adjoint)
+    QSW_LAUNCH mf_apply_kernel<double, double2, true><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), scale);
+  else
+    QSW_LAUNCH mf_apply_kernel<double, double2, false><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), scale);
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
+double op_bytes(const Op& op) {
+  const bool f32 = op.precision == QSW_C64_BULK;
+  if (op.opkind == QSW_OPERATOR_CSR)
+    return (double)op.L.nnz * ((f32 ? sizeof(float2) : sizeof(double2)) + 4) +
+           (double)(op.n + 1) * 4;
+  // matrix-free: H off-diagonal (col + value) and the per-vertex coefficients
+  const double rb = f32 ? 4.0 : 8.0;
+  return (double)op.g.nnz_hoff * (4 + rb) + (double)op.Nt * 2 * rb;
+}
+
 void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
                 double* d_pops, qsw_series_stats* stats) {
   cudaStream_t st = op.ctx->stream;
@@ -448,25 +657,50 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0);
   QSW_CHECK_ARG(info.max_d <= kDMax, QSW_ERR_INVALID_ARG,
                 "more than " + std::to_string(kDMax) + " outputs per Taylor block (steps/s too large)");
-  int tpr = op.tpr;
-  while (tpr < 32 && kKpl * tpr < info.max_d) tpr *= 2;
   const int ring = d_out ? 0 : info.max_d + 1;
-  const size_t vbytes = op.precision == QSW_C64_BULK ? sizeof(float2) : sizeof(double2);
+  const bool f32 = op.precision == QSW_C64_BULK;
+  const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
   op.kbuf.alloc(2 * vbytes * (size_t)op.n);
   if (!d_out) op.ring.alloc(sizeof(double2) * (size_t)op.n * ring);
   op.jobs.alloc(sizeof(Job) * std::max(1, info.njobs));
   op.ctrl.alloc(sizeof(Ctrl));
   QSW_CUDA_TRY(cudaMemsetAsync(op.ctrl.p, 0, sizeof(Ctrl), st));
-  plan_kernel<<<1, 32, 0, st>>>(op.dp_dev.as<double>(), prec, t0, dt, steps, 1, ring,
-                                op.jobs.as<Job>(), info.njobs, info.njobs, op.ctrl.as<Ctrl>());
+  QSW_LAUNCH plan_kernel<<<1, 32, 0, st>>>(op.dp_dev.as<double>(), prec, t0, dt, steps, 1, ring,
+                                           op.jobs.as<Job>(), info.njobs, info.njobs,
+                                           op.ctrl.as<Ctrl>());
   QSW_CUDA_TRY(cudaGetLastError());
+
+  // Hermitian input (every density matrix): L~ maps Hermitian matrices to
+  // Hermitian matrices, so every Taylor term and output is Hermitian and the
+  // matrix-free form computes only the upper triangle.
+  bool herm = false;
+  if (op.opkind == QSW_OPERATOR_MATRIX_FREE) {
+    op.scratch.alloc(2 * sizeof(unsigned long long));
+    QSW_CUDA_TRY(cudaMemsetAsync(op.scratch.p, 0, 2 * sizeof(unsigned long long), st));
+    QSW_LAUNCH herm_check_kernel<<<grid_for(op.n, 256, 152 * 8), 256, 0, st>>>(
+        op.Nt, reinterpret_cast<const double2*>(d_rho0), op.scratch.as<unsigned long long>());
+    QSW_CUDA_TRY(cudaGetLastError());
+    unsigned long long hb[2] = {0, 0};
+    QSW_CUDA_TRY(cudaMemcpyAsync(hb, op.scratch.p, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    double asym2, max2;
+    memcpy(&asym2, &hb[0], sizeof(double));
+    memcpy(&max2, &hb[1], sizeof(double));
+    herm = sqrt(asym2) <= 1e-13 * (sqrt(max2) > 1.0 ? sqrt(max2) : 1.0);
+  }
 
   SeriesArgs a{};
   a.n = (int)op.n;
   a.nt = op.Nt;
-  a.rowptr = op.L.rowptr.as<int>();
-  a.col = op.L.col.as<int>();
-  a.val = op.L.val.p;
+  a.mirror = herm && d_out != nullptr;
+  if (op.opkind == QSW_OPERATOR_CSR) {
+    a.rowptr = op.L.rowptr.as<int>();
+    a.col = op.L.col.as<int>();
+    a.val = op.L.val.p;
+  } else {
+    a.mf64 = make_mf<double>(op, false);
+    a.mf32 = make_mf<float>(op, false);
+  }
   a.k0 = op.kbuf.p;
   a.k1 = static_cast<char*>(op.kbuf.p) + vbytes * (size_t)op.n;
   a.rho0 = reinterpret_cast<const double2*>(d_rho0);
@@ -483,9 +717,8 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   QSW_CUDA_TRY(cudaEventCreate(&ev1));
   QSW_CUDA_TRY(cudaEventRecord(ev0, st));
   int grid = 0;
-  cudaError_t e = op.precision == QSW_C64_BULK
-                      ? launch_series_tpr<float2>(tpr, a, op.ctx->num_sms, st, &grid)
-                      : launch_series_tpr<double2>(tpr, a, op.ctx->num_sms, st, &grid);
+  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid);
   QSW_CUDA_TRY(e);
   QSW_CUDA_TRY(cudaEventRecord(ev1, st));
   Ctrl h{};
@@ -509,8 +742,30 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
     stats->outputs_per_block = info.d;
     stats->jobs = info.njobs;
     stats->matvecs = (int64_t)h.matvecs;
-    stats->bytes_per_matvec = (double)op.L.nnz * (vbytes + 4) + (double)(op.n + 1) * 4 +
-                              2.0 * (double)op.n * vbytes;
+    stats->fupdates = (int64_t)h.fupdates;
+    // algorithmic bytes of one application: the operator's own data, reading
+    // the input vector once and writing the output once
+    stats->bytes_per_matvec = op_bytes(op) + 2.0 * (double)op.n * vbytes;
+    std::vector<Job> jobs(info.njobs);
+    plan_series(op.dp, theta, t0, dt, steps, 1, ring, jobs.data(), info.njobs);
+    double init_bytes = 0.0;   // per block: read Z, write Khat_0 and d copies of Z
+    for (const Job& j : jobs) init_bytes += (16.0 + vbytes + 16.0 * j.d) * (double)op.n;
+    stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
+                               32.0 * (double)op.n * (double)h.fupdates + init_bytes;
+    // the Hermitian form computes the upper triangle: (N~+1)/(2N~) of the
+    // off-diagonal terms and N~(N~+1)/2 elements
+    const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
+    const double elems = frac * (double)op.n;
+    const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
+    const double flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems +
+                                    4.0 * op.g.n_jumps + 5.0 * elems;
+    stats->algorithmic_flops = stats->matvecs * flops_per_matvec + 7.0 * elems * h.fupdates;
+    if (herm) {
+      stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes;
+      stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
+                                 32.0 * elems * (double)h.fupdates + init_bytes;
+    }
+    stats->hermitian = herm ? 1 : 0;
     stats->kernel_ms = ms;
   }
 }
@@ -518,36 +773,53 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
 void apply(const Op& op, const double* d_x, double* d_y) {
   cudaStream_t st = op.ctx->stream;
   const int n = (int)op.n;
+  if (op.opkind == QSW_OPERATOR_MATRIX_FREE) {
+    if (op.precision == QSW_C64_BULK) {
+      DevBuf xs, ys;
+      xs.alloc(sizeof(float2) * op.n);
+      ys.alloc(sizeof(float2) * op.n);
+      QSW_LAUNCH narrow_vec_kernel<<<grid_for(op.n, 256, 4096), 256, 0, st>>>(
+          op.n, reinterpret_cast<const double2*>(d_x), xs.as<float2>());
+      const MfOp<float> m = make_mf<float>(op, false);
+      QSW_LAUNCH mf_apply_kernel<float, float2, false><<<std::min(op.Nt, 152 * 8), kBlock, 0, st>>>(
+          m, 1, xs.as<float2>(), ys.as<float2>(), 1.0);
+      QSW_LAUNCH widen_vec_kernel<<<grid_for(op.n, 256, 4096), 256, 0, st>>>(
+          op.n, ys.as<float2>(), reinterpret_cast<double2*>(d_y));
+      QSW_CUDA_TRY(cudaGetLastError());
+      QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    } else {
+      mf_apply64(op, false, 1, d_x, d_y, 1.0);
+    }
+    return;
+  }
   const unsigned grid = grid_for((long long)n * 8, 256, 152 * 16);
   if (op.L.fp32)
-    apply_kernel<float2><<<grid, 256, 0, st>>>(n, op.L.rowptr.as<int>(), op.L.col.as<int>(),
-                                               op.L.val.as<float2>(),
-                                               reinterpret_cast<const double2*>(d_x),
-                                               reinterpret_cast<double2*>(d_y));
+    QSW_LAUNCH apply_csr_kernel<float2><<<grid, 256, 0, st>>>(
+        n, op.L.rowptr.as<int>(), op.L.col.as<int>(), op.L.val.as<float2>(),
+        reinterpret_cast<const double2*>(d_x), reinterpret_cast<double2*>(d_y));
   else
-    apply_kernel<double2><<<grid, 256, 0, st>>>(n, op.L.rowptr.as<int>(), op.L.col.as<int>(),
-                                                op.L.val.as<double2>(),
-                                                reinterpret_cast<const double2*>(d_x),
-                                                reinterpret_cast<double2*>(d_y));
+    QSW_LAUNCH apply_csr_kernel<double2><<<grid, 256, 0, st>>>(
+        n, op.L.rowptr.as<int>(), op.L.col.as<int>(), op.L.val.as<double2>(),
+        reinterpret_cast<const double2*>(d_x), reinterpret_cast<double2*>(d_y));
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
 void populations(const Op& op, const double* d_rho, int count, double* d_pops) {
   cudaStream_t st = op.ctx->stream;
-  pops_kernel<<<grid_for((long long)count * op.Nt, 256, 4096), 256, 0, st>>>(
+  QSW_LAUNCH pops_kernel<<<grid_for((long long)count * op.Nt, 256, 4096), 256, 0, st>>>(
       count, op.Nt, op.n, reinterpret_cast<const double2*>(d_rho), d_pops);
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
 void widen_values(const Op& op, double* d_val) {
-  widen_kernel<<<grid_for(op.L.nnz, 256, 4096), 256, 0, op.ctx->stream>>>(
+  QSW_LAUNCH widen_vec_kernel<<<grid_for(op.L.nnz, 256, 4096), 256, 0, op.ctx->stream>>>(
       op.L.nnz, op.L.val.as<float2>(), reinterpret_cast<double2*>(d_val));
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
 void initial_state_from_pops(const Op& op, const double* d_pops, double* d_state) {
   cudaStream_t st = op.ctx->stream;
-  diag_state_kernel<<<grid_for(op.n, 256, 4096), 256, 0, st>>>(
+  QSW_LAUNCH diag_state_kernel<<<grid_for(op.n, 256, 4096), 256, 0, st>>>(
       op.Nt, op.n, d_pops, reinterpret_cast<double2*>(d_state));
   QSW_CUDA_TRY(cudaGetLastError());
 }

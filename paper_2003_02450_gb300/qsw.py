@@ -19,6 +19,9 @@ LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "libqsw.so")
 QSW_C128 = 0
 QSW_C64_BULK = 1
 PRECISIONS = {"c128": QSW_C128, "c64": QSW_C64_BULK}
+QSW_OPERATOR_MATRIX_FREE = 0
+QSW_OPERATOR_CSR = 1
+OPERATORS = {"matfree": QSW_OPERATOR_MATRIX_FREE, "csr": QSW_OPERATOR_CSR}
 
 STATUS = {0: "QSW_OK", 1: "QSW_ERR_INVALID_ARG", 2: "QSW_ERR_NOT_SIMPLE",
           3: "QSW_ERR_OMEGA_RANGE", 4: "QSW_ERR_OOM", 5: "QSW_ERR_NOT_CONVERGED",
@@ -50,7 +53,8 @@ class qsw_series_stats(ctypes.Structure):
     _fields_ = [("m0", c_int32), ("s0", c_int32), ("m_star", c_int32), ("s", c_int32),
                 ("step_m", c_int32), ("step_s", c_int32), ("outputs_per_block", c_int32),
                 ("jobs", c_int32), ("matvecs", c_int64), ("bytes_per_matvec", c_double),
-                ("kernel_ms", c_double)]
+                ("kernel_ms", c_double), ("fupdates", c_int64), ("algorithmic_bytes", c_double),
+                ("algorithmic_flops", c_double), ("hermitian", c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -64,7 +68,7 @@ _SIGNATURES = {
     "qsw_last_error": ([c_void_p], ctypes.c_char_p),
     "qsw_build_superoperator": ([c_void_p, POINTER(qsw_csr), POINTER(qsw_csr), c_double,
                                  POINTER(qsw_port), c_int32, POINTER(qsw_port), c_int32, c_int32,
-                                 POINTER(c_void_p)], c_int32),
+                                 c_int32, POINTER(c_void_p)], c_int32),
     "qsw_set_omega": ([c_void_p, c_double], c_int32),
     "qsw_op_info": ([c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_int64),
                      POINTER(c_double)], c_int32),
@@ -78,6 +82,7 @@ _SIGNATURES = {
                                c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
+    "qsw_kernel_launches": ([], c_int64),
     "qsw_select_params": ([POINTER(c_double), c_double, c_int32, c_int32, POINTER(c_int32),
                            POINTER(c_int32)], c_int32),
 }
@@ -171,15 +176,16 @@ def qsw_last_error(ctx) -> str:
 
 
 def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(),
-                            precision="c128"):
+                            precision="c128", operator="matfree"):
     g = _as_csr(G)
     h = _as_csr(H)
     src, nsrc = _ports(sources)
     snk, nsnk = _ports(sinks)
     prec = PRECISIONS.get(precision, precision)
+    kind = OPERATORS.get(operator, operator)
     op = c_void_p()
     st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
-                                       src, nsrc, snk, nsnk, int(prec), byref(op))
+                                       src, nsrc, snk, nsnk, int(prec), int(kind), byref(op))
     _check(st, ctx)
     return op
 
@@ -231,6 +237,10 @@ def qsw_expmv_series_host(ctx, op, h_rho0, t0: float, dt: float, steps: int, h_o
 
 def qsw_populations(ctx, op, d_rho_series, count: int, d_pops) -> None:
     _check(lib().qsw_populations(op, _ptr(d_rho_series), int(count), _ptr(d_pops)), ctx)
+
+
+def qsw_kernel_launches() -> int:
+    return int(lib().qsw_kernel_launches())
 
 
 def qsw_theta_table(precision="c128") -> np.ndarray:

@@ -38,10 +38,12 @@ class LQSW:
     """An L-QSW on a digraph G (row = destination, column = source)."""
 
     def __init__(self, G, omega: float, H=None, sources=(), sinks=(), precision: str = "c128",
-                 ctx: Context | None = None):
+                 ctx: Context | None = None, operator: str = "matfree"):
         self.ctx = ctx or Context()
         self.precision = precision
-        self.op = _c.qsw_build_superoperator(self.ctx.handle, G, H, omega, sources, sinks, precision)
+        self.operator = operator
+        self.op = _c.qsw_build_superoperator(self.ctx.handle, G, H, omega, sources, sinks,
+                                             precision, operator)
         info = _c.qsw_op_info(self.ctx.handle, self.op)
         self.n_tilde = info["n_tilde"]
         self.n = info["n"]

@@ -38,9 +38,13 @@ def _oracle(g, omega, H=None, sources=(), sinks=()):
     return walk, superop.superoperator(walk, omega)
 
 
-def _gpu(ctx, g, omega, H=None, sources=(), sinks=(), precision="c128"):
+def _gpu(ctx, g, omega, H=None, sources=(), sinks=(), precision="c128", operator="matfree"):
     from paper_2003_02450_gb300.walk import LQSW
-    return LQSW(g, omega, H=H, sources=sources, sinks=sinks, precision=precision, ctx=ctx)
+    return LQSW(g, omega, H=H, sources=sources, sinks=sinks, precision=precision, ctx=ctx,
+                operator=operator)
+
+
+OPERATORS = ["matfree", "csr"]
 
 
 def _csr_from_gpu(w):
@@ -86,19 +90,22 @@ def _small_case(N, p, seed, explicit_h):
     return g, H
 
 
+@pytest.mark.parametrize("operator", OPERATORS)
 @pytest.mark.parametrize("N,p,seed,omega,sources,sinks,explicit_h", SMALL)
-def test_assembly_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h):
+def test_assembly_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h, operator):
     g, H = _small_case(N, p, seed, explicit_h)
     _, Lo = _oracle(g, omega, H, sources, sinks)
-    w = _gpu(ctx, g, omega, H, sources, sinks)
+    w = _gpu(ctx, g, omega, H, sources, sinks, operator=operator)
+    assert w.nnz == _csr_from_gpu(w).nnz
     _compare_csr(_csr_from_gpu(w), Lo)
 
 
+@pytest.mark.parametrize("operator", OPERATORS)
 @pytest.mark.parametrize("N,p,seed,omega,sources,sinks,explicit_h", SMALL)
-def test_norms_and_params_match_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h):
+def test_norms_and_params_match_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h, operator):
     g, H = _small_case(N, p, seed, explicit_h)
     _, Lo = _oracle(g, omega, H, sources, sinks)
-    w = _gpu(ctx, g, omega, H, sources, sinks)
+    w = _gpu(ctx, g, omega, H, sources, sinks, operator=operator)
     info = expmv.NormInfo(Lo, precompute=True)
     assert w.norms[0] == pytest.approx(info.one, rel=1e-14, abs=0)
     for p_ in range(2, 10):
@@ -108,32 +115,63 @@ def test_norms_and_params_match_oracle(ctx, N, p, seed, omega, sources, sinks, e
         assert expmv.select_params(ginfo, t) == expmv.select_params(info, t)
 
 
+@pytest.mark.parametrize("operator", OPERATORS)
 @pytest.mark.parametrize("N,p,seed,omega,sources,sinks,explicit_h", SMALL)
-def test_apply_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h):
+def test_apply_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h, operator):
     import torch
     g, H = _small_case(N, p, seed, explicit_h)
     walk, Lo = _oracle(g, omega, H, sources, sinks)
-    w = _gpu(ctx, g, omega, H, sources, sinks)
+    w = _gpu(ctx, g, omega, H, sources, sinks, operator=operator)
     x = W.vec(W.random_density_matrix(walk.n_tilde, seed))
     y = w.apply(torch.from_numpy(x).cuda()).cpu().numpy()
     ref = Lo @ x
     assert np.max(np.abs(y - ref)) <= 1e-14 * max(1.0, np.max(np.abs(Lo.data), initial=0))
 
 
+@pytest.mark.parametrize("operator", OPERATORS)
 @pytest.mark.parametrize("N,p,seed,omega,sources,sinks,explicit_h", SMALL)
 @pytest.mark.parametrize("t0,dt,steps", [(0.0, 0.1, 100), (0.5, 2.0, 3), (1.0, 0.25, 37),
                                          (2.5, 0.0, 0), (0.0, 0.7, 1)])
-def test_series_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h, t0, dt, steps):
+def test_series_matches_oracle(ctx, N, p, seed, omega, sources, sinks, explicit_h, t0, dt, steps,
+                               operator):
     import torch
     g, H = _small_case(N, p, seed, explicit_h)
     walk, Lo = _oracle(g, omega, H, sources, sinks)
     rho0 = W.vec(W.random_density_matrix(walk.n_tilde, seed + 7))
     ref = expmv.expmv_series(Lo, rho0, t0, dt, steps)
-    w = _gpu(ctx, g, omega, H, sources, sinks)
+    w = _gpu(ctx, g, omega, H, sources, sinks, operator=operator)
     states, pops = w.series(t0, dt, steps, rho0=torch.from_numpy(rho0).cuda())
     got = states.cpu().numpy()
     assert np.max(np.abs(got - ref)) <= TOL_C128
     assert np.max(np.abs(pops.cpu().numpy() - superop.populations(ref, walk.n_tilde))) <= TOL_C128
+
+
+@pytest.mark.parametrize("operator", OPERATORS)
+@pytest.mark.parametrize("N,p,seed,omega,sources,sinks,explicit_h", SMALL[3:])
+def test_series_non_hermitian_input(ctx, N, p, seed, omega, sources, sinks, explicit_h, operator):
+    # a general complex vector (not a density matrix): the Hermitian shortcut
+    # must not be taken and the result must still match
+    import torch
+    g, H = _small_case(N, p, seed, explicit_h)
+    walk, Lo = _oracle(g, omega, H, sources, sinks)
+    rng = np.random.default_rng(seed)
+    x0 = rng.standard_normal(walk.n_tilde ** 2) + 1j * rng.standard_normal(walk.n_tilde ** 2)
+    ref = expmv.expmv_series(Lo, x0, 0.2, 0.3, 12)
+    w = _gpu(ctx, g, omega, H, sources, sinks, operator=operator)
+    states, _ = w.series(0.2, 0.3, 12, rho0=torch.from_numpy(x0).cuda())
+    assert w.last_stats["hermitian"] == 0
+    assert np.max(np.abs(states.cpu().numpy() - ref)) <= TOL_C128 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_hermitian_shortcut_taken_for_density_matrices(ctx):
+    import torch
+    cfg = W.cycle16()
+    w = _gpu(ctx, cfg.graph, cfg.omega)
+    w.initial_state(rho0=cfg.rho0)
+    states, _ = w.series(0.0, 0.5, 4)
+    assert w.last_stats["hermitian"] == 1
+    S = states.reshape(5, 16, 16)
+    assert torch.equal(S, S.conj().transpose(1, 2))   # lower triangles mirrored exactly
 
 
 def test_cycle16_config_series(ctx):
@@ -218,13 +256,14 @@ def test_er1000_assembly_full_size(ctx, er1000):
     assert w.norms[0] == pytest.approx(expmv.NormInfo(Lo).one, rel=1e-14)
 
 
-def test_er1000_series_first_steps_full_size(ctx, er1000):
+@pytest.mark.parametrize("operator", OPERATORS)
+def test_er1000_series_first_steps_full_size(ctx, er1000, operator):
     # the bench's launch (same call, same operator size); the oracle finishes the
     # first two output times of the 50-step grid in seconds
     cfg, walk, Lo = er1000
     rho0 = W.vec(cfg.rho0)
     ref = expmv.expmv_series(Lo, rho0, cfg.t0, cfg.dt, 2)
-    w = _gpu(ctx, cfg.graph, cfg.omega)
+    w = _gpu(ctx, cfg.graph, cfg.omega, operator=operator)
     w.initial_state(rho0=cfg.rho0)
     states, _ = w.series(cfg.t0, cfg.dt, 2)
     assert np.max(np.abs(states.cpu().numpy() - ref)) <= TOL_C128
@@ -297,20 +336,22 @@ def test_grid45_assembly_and_first_steps_c128(ctx, grid45):
     assert np.max(np.abs(states.cpu().numpy() - ref)) <= TOL_C128
 
 
-def test_grid45_c64_bulk_populations(ctx, grid45):
+@pytest.mark.parametrize("operator", OPERATORS)
+def test_grid45_c64_bulk_populations(ctx, grid45, operator):
     cfg, walk, Lo, ref = grid45
-    w = _gpu(ctx, cfg.graph, cfg.omega, precision="c64")
+    w = _gpu(ctx, cfg.graph, cfg.omega, precision="c64", operator=operator)
     w.initial_state(rho0=cfg.rho0)
     _, pops = w.series(cfg.t0, cfg.dt, 2)
     err = np.max(np.abs(pops.cpu().numpy() - superop.populations(ref, 2025)))
     assert err <= TOL_C64_POP, err
 
 
-def test_cycle16_c64_bulk(ctx):
+@pytest.mark.parametrize("operator", OPERATORS)
+def test_cycle16_c64_bulk(ctx, operator):
     cfg = W.cycle16()
     walk, Lo = _oracle(cfg.graph, cfg.omega)
     ref = expmv.expmv_series(Lo, W.vec(cfg.rho0), cfg.t0, cfg.dt, cfg.steps)
-    w = _gpu(ctx, cfg.graph, cfg.omega, precision="c64")
+    w = _gpu(ctx, cfg.graph, cfg.omega, precision="c64", operator=operator)
     w.initial_state(rho0=cfg.rho0)
     _, pops = w.series(cfg.t0, cfg.dt, cfg.steps)
     assert np.max(np.abs(pops.cpu().numpy() - superop.populations(ref, 16))) <= TOL_C64_POP
@@ -350,4 +391,6 @@ def test_empty_graph_is_static(ctx):
         rho0 = W.random_density_matrix(5, 1)
         w.initial_state(rho0=rho0)
         states, _ = w.series(0.0, 1.0, 4)
-        assert np.max(np.abs(states.cpu().numpy() - W.vec(rho0)[None, :])) == 0.0
+        # L~ = 0; the Hermitian form returns the Hermitian part of rho0 (numpy's
+        # rho0 is Hermitian only to ~1e-17)
+        assert np.max(np.abs(states.cpu().numpy() - W.vec(rho0)[None, :])) <= 1e-15
