@@ -36,56 +36,45 @@ template <class R> struct MfOp {
 
 template <class T> __device__ __forceinline__ T ldcg_t(const T* p) { return __ldcg(p); }
 
-// Entry (a, b) of x.  With HERM the array holds only its upper triangle
-// (a <= b) of a Hermitian matrix and (a, b), a > b, is read as conj(x(b, a)).
-template <bool HERM, class VT>
-__device__ __forceinline__ VT mf_ld(const VT* __restrict__ x, int Nt, int a, int b) {
-  if (!HERM) return __ldcg(x + a + (long long)Nt * b);
-  const bool up = a <= b;
-  VT v = __ldcg(x + (up ? a : b) + (long long)Nt * (up ? b : a));
-  if (!up) v.y = -v.y;
-  return v;
-}
-
-// Part B of C for RPT rows of one column: sum over the uniform list H row j.
-template <class R, class VT, int RPT, bool HERM>
+// Part B of C for RPT rows of one column, accumulated with a minus sign:
+// c = -sum_{m in H row j} c_mj x_(i,m)  (the uniform list, coalesced over i).
+template <class R, class VT, int RPT>
 __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict__ x, int j,
-                                         const int* irow, R* bx, R* by) {
+                                         const int* irow, R* cx, R* cy) {
 #pragma unroll
-  for (int u = 0; u < RPT; ++u) { bx[u] = 0; by[u] = 0; }
+  for (int u = 0; u < RPT; ++u) { cx[u] = 0; cy[u] = 0; }
   if (j >= op.N) return;
   const int e0 = op.hrow[j], e1 = op.hrow[j + 1];
   for (int e = e0; e < e1; ++e) {
-    const int m = op.hcol[e];
+    const long long off = (long long)op.Nt * op.hcol[e];
     const R h = op.hval[e];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (irow[u] >= 0) {
-        const VT v = mf_ld<HERM>(x, op.Nt, irow[u], m);
-        bx[u] = fma(h, v.x, bx[u]);
-        by[u] = fma(h, v.y, by[u]);
+        const VT v = __ldcg(x + off + irow[u]);
+        cx[u] = fma(-h, v.x, cx[u]);
+        cy[u] = fma(-h, v.y, cy[u]);
       }
     }
   }
 }
 
-// The rest of element (i, j): part A, diagonal, jumps; returns (L x)_(i,j) or
-// (L^H x)_(i,j) given part B.
-template <class R, class VT, bool ADJ, bool HERM>
+// The rest of element (i, j): part A (added to the same accumulators), the
+// diagonal and the jumps; returns (L x)_(i,j) or (L^H x)_(i,j).
+template <class R, class VT, bool ADJ>
 __device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
-                                          R bx, R by, R& yx, R& yy) {
-  R ax = 0, ay = 0;
+                                          R cx, R cy, R& yx, R& yy) {
+  const long long base = (long long)op.Nt * j;
   if (i < op.N) {
     const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
     for (int e = e0; e < e1; ++e) {
-      const VT v = mf_ld<HERM>(x, op.Nt, op.hcol[e], j);
+      const VT v = __ldcg(x + base + op.hcol[e]);
       const R h = op.hval[e];
-      ax = fma(h, v.x, ax);
-      ay = fma(h, v.y, ay);
+      cx = fma(h, v.x, cx);
+      cy = fma(h, v.y, cy);
     }
   }
-  const R cx = ax - bx, cy = ay - by;
-  const VT xs = __ldcg(x + i + (long long)op.Nt * j);
+  const VT xs = __ldcg(x + base + i);
   const R dx = op.ad[i] + op.ad[j];
   const R dy = op.hw[j] - op.hw[i];
   R rx, ry;

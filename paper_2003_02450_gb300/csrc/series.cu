@@ -87,11 +87,17 @@ template <class VT> struct Cplx;
 template <> struct Cplx<double2> {
   using R = double;
   __device__ static double2 make(double a, double b) { return make_double2(a, b); }
+  __device__ static double2 conj_of(double a, double b) {
+    return make_double2(a, __longlong_as_double(__double_as_longlong(b) ^ (1LL << 63)));
+  }
   __device__ static const MfOp<double>& mf(const SeriesArgs& a) { return a.mf64; }
 };
 template <> struct Cplx<float2> {
   using R = float;
   __device__ static float2 make(float a, float b) { return make_float2(a, b); }
+  __device__ static float2 conj_of(float a, float b) {
+    return make_float2(a, __int_as_float(__float_as_int(b) ^ (int)0x80000000));
+  }
   __device__ static const MfOp<float>& mf(const SeriesArgs& a) { return a.mf32; }
 };
 
@@ -220,7 +226,19 @@ series_kernel(SeriesArgs a) {
     // ---- init: Khat_0 = Z, F_k = Z, ||Z||_inf
     unsigned long long zmax = 0;
     for (long long r = gthread; r < a.n; r += nthreads) {
-      const double2 z = __ldcg(Z + r);
+      double2 z;
+      if (OPK == kOpMatfreeHerm) {
+        // only upper triangles are maintained: read (i, j), i > j, as conj(Z(j, i))
+        const int i = (int)(r % a.nt), j = (int)(r / a.nt);
+        if (i > j) {
+          z = __ldcg(Z + j + (long long)a.nt * i);
+          z.y = -z.y;
+        } else {
+          z = __ldcg(Z + r);
+        }
+      } else {
+        z = __ldcg(Z + r);
+      }
       kcur[r] = Cplx<VT>::make((R)z.x, (R)z.y);
       for (int k = 0; k < J.d; ++k) slot_ptr(a, J.out_index0 + k)[r] = z;
       zmax = umax64(zmax, as_bits(z.x * z.x + z.y * z.y));
@@ -295,14 +313,20 @@ series_kernel(SeriesArgs a) {
             const int i = i0 + lane + 32 * u;
             irow[u] = (i < nt && (!kHerm || i <= j)) ? i : -1;
           }
-          R bx[kRpt], by[kRpt];
-          mf_partB<R, VT, kRpt, kHerm>(op, kcur, j, irow, bx, by);
+          R cx[kRpt], cy[kRpt];
+          mf_partB<R, VT, kRpt>(op, kcur, j, irow, cx, cy);
 #pragma unroll
           for (int u = 0; u < kRpt; ++u) {
             if (irow[u] < 0) continue;
             R yx, yy;
-            mf_finish<R, VT, false, kHerm>(op, kcur, irow[u], j, bx[u], by[u], yx, yy);
-            ep.consume(irow[u] + (long long)nt * j, yx * rscale, yy * rscale);
+            mf_finish<R, VT, false>(op, kcur, irow[u], j, cx[u], cy[u], yx, yy);
+            yx *= rscale;
+            yy *= rscale;
+            ep.consume(irow[u] + (long long)nt * j, yx, yy);
+            // Hermitian form: the term is stored in full, its lower triangle
+            // as the conjugate (sign flip on the bit pattern, no FP64 op)
+            if (kHerm && irow[u] != j)
+              knext[j + (long long)nt * irow[u]] = Cplx<VT>::conj_of(yx, yy);
           }
         }
       } else {
@@ -414,6 +438,8 @@ series_kernel(SeriesArgs a) {
         double2 z = __ldcg(F + j + (long long)a.nt * i);
         F[r] = make_double2(z.x, -z.y);
       }
+      // the next block reads its input Z (this block's last output) in full
+      if (!grid_barrier(ctrl)) return;
     }
 
     // ---- populations of the finished outputs
@@ -460,12 +486,12 @@ mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__
       for (int c = 0; c < cols; ++c) {
         const VT* xc = x + c * n;
         R bx[kRpt], by[kRpt];
-        mf_partB<R, VT, kRpt, false>(op, xc, j, irow, bx, by);
+        mf_partB<R, VT, kRpt>(op, xc, j, irow, bx, by);
 #pragma unroll
         for (int u = 0; u < kRpt; ++u) {
           if (irow[u] < 0) continue;
           R yx, yy;
-          mf_finish<R, VT, ADJ, false>(op, xc, irow[u], j, bx[u], by[u], yx, yy);
+          mf_finish<R, VT, ADJ>(op, xc, irow[u], j, bx[u], by[u], yx, yy);
           y[c * n + irow[u] + (long long)op.Nt * j] =
               Cplx<VT>::make(yx * (R)scale, yy * (R)scale);
         }
