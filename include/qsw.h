@@ -7,7 +7,7 @@
  *     rho~(t_k) = exp(t_k L~) rho~(0),   t_k = t0 + k dt,  k = 0..steps,
  *
  * where L~ is the N~^2 x N~^2 vectorised superoperator of the master equation
- * (paper: QSW_MPI, arXiv:2003.02450, Section 2.4, Eqs. qsw, qsw_ss,
+ * (paper: QSW_MPI, arXiv:2003.02450, Section 2.5, Eqs. qsw, qsw_ss,
  * vec_mappings, qsw_vec_sol), computed by Al-Mohy & Higham's truncated-Taylor
  * scaling-and-squaring algorithms (paper Section 3.1: Algorithm 3.2 `step`,
  * Algorithm 5.2 `series`, parameters from the 1-norm series of L~ that is
@@ -21,9 +21,9 @@
  *   orientation).  Columns strictly increasing within a row, no self-loops
  *   (simple graphs, Tr G = 0), weights finite and > 0.  Graph arrays are HOST
  *   pointers; the library copies them.
- * - Vectorisation is column-major: rho~[i + N~ j] = rho[i][j] (Section 2.4.3).
+ * - Vectorisation is column-major: rho~[i + N~ j] = rho[i][j] (Section 2.5.3).
  *   Sources, then sinks, are appended after the N graph vertices, in argument
- *   order, so N~ = N + n_sources + n_sinks (Section 2.4.1).
+ *   order, so N~ = N + n_sources + n_sinks (Section 2.5.1).
  * - Complex numbers are interleaved (re, im) pairs of doubles: a state vector
  *   of n = N~^2 entries occupies 2n doubles (16 n bytes).
  * - "d_" arguments are DEVICE pointers on the context's device, owned by the
@@ -86,7 +86,7 @@ typedef struct {
 } qsw_csr;
 
 /* A source (feeding `vertex`) or a sink (draining `vertex`) with its rate
- * Gamma or Theta (Section 2.4.1, Eq. qsw_ss).  The rate multiplies a unit
+ * Gamma or Theta (Section 2.5.1, Eq. qsw_ss).  The rate multiplies a unit
  * jump operator and is not scaled by omega. */
 typedef struct {
   int32_t vertex;
@@ -132,7 +132,7 @@ const char* qsw_last_error(const qsw_ctx* ctx);
 
 /* ---------------------------------------------------------- construction */
 
-/* Build L~ for an L-QSW (paper Section 2.4, Eq. qsw_ss; condensed
+/* Build L~ for an L-QSW (paper Section 2.5, Eq. qsw_ss; condensed
  * construction of Section 3.3, Eq. condensed_lindblads).
  *   G        : the digraph (host CSR).  One jump operator sqrt(G_ij)|i><j| per
  *              arc j -> i (Eq. lindblad), weighted by omega.
@@ -215,7 +215,7 @@ qsw_status qsw_expmv_series_host(qsw_op* op, const double* h_rho0, double t0, do
                                  qsw_series_stats* stats);
 
 /* Populations of `count` consecutive states: d_pops[c N~ + i] =
- * Re d_rho_series[c n + i (N~ + 1)] (Section 2.3; `gather_populations`). */
+ * Re d_rho_series[c n + i (N~ + 1)] (Section 2.4; `gather_populations`). */
 qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t count,
                            double* d_pops);
 

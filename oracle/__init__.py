@@ -5,10 +5,10 @@ library computes, written from the paper (QSW_MPI, arXiv:2003.02450) and the
 Al-Mohy--Higham expmv algorithms it names (Section 3.1).  It exists so that the
 CUDA path can be checked against something independent of it:
 
-* ``graph``    -- digraph normalisation (Section 2.1-2.4, Eqs. adjacency_graph,
+* ``graph``    -- digraph normalisation (Section 2.1-2.5, Eqs. adjacency_graph,
                   out_degree, generator_matrix, lindblad, qsw_ss).
 * ``superop``  -- the vectorised superoperator built from explicit Kronecker
-                  products (Section 2.4.3, Eq. vec_mappings, Eq. qsw).
+                  products (Section 2.5.3, Eq. vec_mappings, Eq. qsw).
 * ``theta``    -- theta_m(tol) from its backward-error definition (table made
                   by ``make_theta.py`` with mpmath, stored in theta_tables.json).
 * ``normest``  -- exact ||A^p||_1 and the Higham--Tisseur block estimator.

@@ -12,7 +12,7 @@ Follows Section 2 of the paper:
   Laplacian; the package's ``operators.trans(gamma, GU)``).
 * Eq. lindblad (read as one jump operator per arc, no dephasing term):
   L_k = sqrt(G_ij) |v_i><v_j| for every arc j -> i, weighted by omega in Eq. qsw.
-* Sources and sinks (Section 2.4.1, Eq. qsw_ss): extra vertices appended after
+* Sources and sinks (Section 2.5.1, Eq. qsw_ss): extra vertices appended after
   the N graph vertices (sources first, in argument order, then sinks); a source
   s feeding vertex v adds the jump |v><s| at rate Gamma, a sink z draining v adds
   |z><v| at rate Theta; these terms are not scaled by omega and the extra

@@ -1,7 +1,7 @@
 """The vectorised L-QSW superoperator (oracle; test infrastructure only).
 
-Written from Eq. qsw / Eq. qsw_ss (Section 2.4) and the vectorisation
-identities of Eq. vec_mappings (Section 2.4.3), with column-stacking vec
+Written from Eq. qsw / Eq. qsw_ss (Section 2.5) and the vectorisation
+identities of Eq. vec_mappings (Section 2.5.3), with column-stacking vec
 (index k = i + N~ j, Eq. qsw_vec_sol's rho~_k <-> rho_ij):
 
     [X, Y]     <->  (I (x) X - X^T (x) I) vec(Y)
@@ -75,7 +75,7 @@ def superoperator(walk: Walk, omega: float) -> sp.csr_matrix:
 
 
 def populations(rho_vec: np.ndarray, n_tilde: int) -> np.ndarray:
-    """p_i = Re rho_ii = Re rho~[i + N~ i] (Section 2.3: diagonal entries are
+    """p_i = Re rho_ii = Re rho~[i + N~ i] (Section 2.4: diagonal entries are
     the vertex populations).  Works on one vector or a stack (..., n)."""
     idx = np.arange(n_tilde) * (n_tilde + 1)
     return np.real(np.asarray(rho_vec)[..., idx])

@@ -1,4 +1,4 @@
-// Digraph normalisation on the device (paper Section 2.1-2.4).
+// Digraph normalisation on the device (paper Section 2.1-2.5).
 //
 //   G^T            : transpose of the adjacency (rows = source vertex).
 //   OutDeg(j)      : sum_i G_ij (Eq. out_degree) -- part of the jump rates.

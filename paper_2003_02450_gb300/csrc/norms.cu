@@ -104,16 +104,25 @@ __global__ void colabs_partial_kernel(int n, int t, const double2* __restrict__ 
   }
 }
 
+// Deterministic sum of per-block partials: fixed tree over one block.
 __global__ void sum_partials_kernel(int nparts, const double* __restrict__ partials,
                                     double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double a0 = 0, a1 = 0;
-    for (int b = 0; b < nparts; ++b) {
-      a0 += partials[b * 2];
-      a1 += partials[b * 2 + 1];
+  __shared__ double s0[kRedGrid], s1[kRedGrid];
+  for (int b = threadIdx.x; b < kRedGrid; b += blockDim.x) {
+    s0[b] = b < nparts ? partials[b * 2] : 0.0;
+    s1[b] = b < nparts ? partials[b * 2 + 1] : 0.0;
+  }
+  __syncthreads();
+  for (int o = kRedGrid / 2; o > 0; o >>= 1) {
+    for (int b = threadIdx.x; b < o; b += blockDim.x) {
+      s0[b] += s0[b + o];
+      s1[b] += s1[b + o];
     }
-    out[0] = a0;
-    out[1] = a1;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = s0[0];
+    out[1] = s1[0];
   }
 }
 
@@ -182,13 +191,24 @@ __global__ void argmax_partial_kernel(int n, const double* __restrict__ h, Excl 
 __global__ void argmax_final_kernel(int nparts, const double* __restrict__ pv,
                                     const int* __restrict__ pi, const double* __restrict__ h,
                                     int probe, double* __restrict__ out) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    double bv = 0;
-    int bi = -1;
-    for (int b = 0; b < nparts; ++b)
-      if (better(pv[b], pi[b], bv, bi)) { bv = pv[b]; bi = pi[b]; }
-    out[0] = bv;
-    out[1] = (double)bi;
+  __shared__ double sv[kRedGrid];
+  __shared__ int si[kRedGrid];
+  for (int b = threadIdx.x; b < kRedGrid; b += blockDim.x) {
+    sv[b] = b < nparts ? pv[b] : 0.0;
+    si[b] = b < nparts ? pi[b] : -1;
+  }
+  __syncthreads();
+  for (int o = kRedGrid / 2; o > 0; o >>= 1) {
+    for (int b = threadIdx.x; b < o; b += blockDim.x)
+      if (better(sv[b + o], si[b + o], sv[b], si[b])) {
+        sv[b] = sv[b + o];
+        si[b] = si[b + o];
+      }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = sv[0];
+    out[1] = (double)si[0];
     out[2] = probe >= 0 ? h[probe] : 0.0;
   }
 }
@@ -285,7 +305,7 @@ struct Estimator {
 
   void colnorms(const double2* Yp, double* host2) {
     QSW_LAUNCH colabs_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, t, Yp, partials.as<double>());
-    QSW_LAUNCH sum_partials_kernel<<<1, 32, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
+    QSW_LAUNCH sum_partials_kernel<<<1, 256, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
     QSW_CUDA_TRY(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
   }
@@ -297,7 +317,7 @@ struct Estimator {
     for (int q = 0; q < e.n; ++q) e.idx[q] = ex[q];
     QSW_LAUNCH argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, h.as<double>(), e, pv.as<double>(),
                                                           pi.as<int>());
-    QSW_LAUNCH argmax_final_kernel<<<1, 32, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
+    QSW_LAUNCH argmax_final_kernel<<<1, 256, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
                                           probe, out.as<double>());
     double o[3];
     QSW_CUDA_TRY(cudaMemcpyAsync(o, out.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -307,18 +327,32 @@ struct Estimator {
     if (hprobe) *hprobe = o[2];
   }
 
+  // chain[p-1] = A^p X0 for the common starting block X0, p = 1..pmax: every
+  // estimate's first product comes from this one chain of pmax products.
+  DevBuf chain;
+  void make_chain(int pmax) {
+    const size_t blk = (size_t)n * t;
+    chain.alloc(sizeof(double2) * blk * (pmax + 1));
+    double2* c0 = chain.as<double2>();
+    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, c0);
+    QSW_CUDA_TRY(cudaGetLastError());
+    for (int p = 1; p <= pmax; ++p) mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr);
+  }
+
   double estimate(int p) {
     double2* Xp = X.as<double2>();
     double2* Yp = Y.as<double2>();
     double2* Wp = W.as<double2>();
-    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Xp);
-    QSW_CUDA_TRY(cudaGetLastError());
     std::vector<int> hist;
     double est_old = 0.0, est = 0.0;
     int ind[2] = {0, 0};
     int ind_best = 0;
     for (int k = 1;; ++k) {
-      mult(false, p, Xp, Yp, Wp);
+      if (k == 1)
+        QSW_CUDA_TRY(cudaMemcpyAsync(Yp, chain.as<double2>() + (size_t)n * t * p,
+                                     sizeof(double2) * (size_t)n * t, cudaMemcpyDeviceToDevice, st));
+      else
+        mult(false, p, Xp, Yp, Wp);
       double cn[2] = {0, 0};
       colnorms(Yp, cn);
       const int jbest = (t > 1 && cn[1] > cn[0]) ? 1 : 0;
@@ -407,6 +441,7 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.pv.alloc(sizeof(double) * kRedGrid);
   E.pi.alloc(sizeof(int) * kRedGrid);
   E.out.alloc(sizeof(double) * 4);
+  if (one != 0.0) E.make_chain(kNormPowers);
   for (int p = 2; p <= kNormPowers; ++p) op.norms[p - 1] = one == 0.0 ? 0.0 : E.estimate(p);
 
   // d_p = ||L^p||_1^(1/p), taken on the device; the host keeps a copy for sizing.

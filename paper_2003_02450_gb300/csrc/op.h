@@ -12,7 +12,7 @@ struct qsw_ctx {
 
 namespace qsw {
 
-// Device-side graph data of one walk (Section 2.1-2.4 normalisation).
+// Device-side graph data of one walk (Section 2.1-2.5 normalisation).
 struct GraphDev {
   int N = 0;        // graph vertices
   int Nt = 0;       // N~ = N + sources + sinks

@@ -3,7 +3,7 @@
 Independent references: scipy.linalg.expm on the dense superoperator, the
 values printed in the paper's Section 4 example (tests/golden), the omega = 0
 CTQW and omega = 1 CTRW limits solved in the N x N vertex space
-(tests/pins.py), density-matrix invariants (Section 2.3) and SciPy's own
+(tests/pins.py), density-matrix invariants (Section 2.4) and SciPy's own
 implementation of the same Al-Mohy--Higham algorithm.
 """
 import os
