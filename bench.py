@@ -48,6 +48,9 @@ def parse_args():
                     help="how the series applies the superoperator")
     ap.add_argument("--no-csr-line", action="store_true",
                     help="skip the extra CSR-operator series measurement")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256"],
+                    help="er1000: one walk per step (default); batch256: 256 random 4-regular "
+                         "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run one build + one series of this many output times and exit "
@@ -58,6 +61,23 @@ def parse_args():
 def dist_env():
     return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
             int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def max_over_ranks(x: float, device="cpu") -> float:
+    """Max of a per-rank float over the process group (identity without one)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, steps_per_walk: int, ms_per_step: float) -> float:
+    """Whole-job time-steps/s: every rank runs its own walk (weak scaling), the
+    job's step time is the slowest rank's."""
+    return world * steps_per_walk * 1000.0 / ms_per_step
 
 
 # ------------------------------------------------------------------ oracle --
@@ -227,13 +247,8 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     clocks = sampler.stop()
     launches = (C.qsw_kernel_launches() - l0) / args.steps
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * q * 1000.0 / ms
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, dev)
+    value = job_value(world, q, ms)
 
     kern_ms = statistics.mean(s["kernel_ms"] for s in stats)
     alg_bytes = statistics.mean(s["algorithmic_bytes"] for s in stats)
@@ -278,16 +293,11 @@ def run_ours(args):
         for _ in range(args.steps):
             e2e_step()
         torch.cuda.synchronize(dev)
-        e_ms = (time.perf_counter() - t0) * 1000.0 / args.steps
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, dev)
         g = cfg.graph
         h2d = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + h_rho0.numel() * 16
         d2h = h_out.numel() * 16 + h_pops.numel() * 8
-        e2e = {"value": world * q * 1000.0 / e_ms, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        e2e = {"value": job_value(world, q, e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms,
                "api": "qsw_build_superoperator + qsw_expmv_series_host (host buffers)"}
 
@@ -360,6 +370,82 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_batch_workload(args):
+    """256 random 4-regular walks (N ~ U{16..512}), omega ~ U(0,1), 4 random pure
+    states each, 10 steps of dt = 0.2.  One step = build the 256 operators from
+    the host graphs + one batched series launch (complex64 bulk) with populations.
+    Also times the plain complex128 single-walk form on the same walks (one
+    series call per initial state) for the walks/s comparison."""
+    import numpy as np
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(0, stream.cuda_stream)
+    walks = W.batch_regular()
+    q, dt, n0 = 10, 0.2, 4
+    rhos = [torch.from_numpy(np.concatenate([W.vec(s) for s in st])).to(dev) for _, _, st in walks]
+    pops = [torch.empty((q + 1) * n0 * g.n, dtype=torch.float64, device=dev) for g, _, _ in walks]
+
+    def batch_step():
+        ops = [C.qsw_build_superoperator(ctx, g, None, om, precision="c64", defer_norms=True)
+               for g, om, _ in walks]
+        st = C.qsw_batch_series(ctx, ops, rhos, n0, [0.0] * len(walks), [dt] * len(walks),
+                                [q] * len(walks), pops)
+        for o in ops:
+            C.qsw_op_destroy(o)
+        return st
+
+    for _ in range(max(1, args.warmup)):
+        batch_step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = C.qsw_kernel_launches()
+    ev0.record(stream)
+    stats = [batch_step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (C.qsw_kernel_launches() - l0) / args.steps
+
+    # plain complex128 single-walk form: one op per walk, one series per state
+    out1 = {g.n: torch.empty((q + 1) * g.n, dtype=torch.float64, device=dev) for g, _, _ in walks}
+    def single_step():
+        for (g, om, st), rho in zip(walks, rhos):
+            op = C.qsw_build_superoperator(ctx, g, None, om, precision="c128")
+            n = g.n * g.n
+            for c in range(n0):
+                C.qsw_expmv_series(ctx, op, rho[c * n:(c + 1) * n], 0.0, dt, q, None, out1[g.n])
+            C.qsw_op_destroy(op)
+    single_step()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    single_step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    single_ms = e0.elapsed_time(e1)
+    C.qsw_destroy(ctx)
+    s0 = stats[-1]
+    line = {"metric": "walks/s (256 random 4-regular walks x 4 pure states, 10 steps, batched)",
+            "value": len(walks) * 1000.0 / ms, "unit": "walks/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "c64 bulk (complex64 terms, FP64 Taylor sums / norms / (m,s))",
+            "data": "synthetic (seeded random 4-regular graphs)",
+            "config": {"workload": "batch256", "walks": len(walks), "rhs_per_walk": n0,
+                       "steps": q, "dt": dt, "clusters": s0["clusters"]},
+            "batch": {"norms_ms": s0["norms_ms"], "series_ms": s0["series_ms"],
+                      "matvecs": s0["matvecs"], "fupdates": s0["fupdates"]},
+            "single_walk_c128": {"ms": single_ms, "walks_per_s": len(walks) * 1000.0 / single_ms},
+            "gpu_launches": launches, "clocks": clocks}
+    print(json.dumps(line))
+
+
 def run_profile_case(q: int):
     import torch
     from paper_2003_02450_gb300 import qsw as C
@@ -387,6 +473,9 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "batch256":
+        run_batch_workload(args)
         return
     run_ours(args)
 

@@ -73,6 +73,11 @@ typedef enum { QSW_C128 = 0, QSW_C64_BULK = 1 } qsw_precision;
  * QSW_OPERATOR_CSR: the assembled CSR superoperator (Section 3.2-3.3). */
 typedef enum { QSW_OPERATOR_MATRIX_FREE = 0, QSW_OPERATOR_CSR = 1 } qsw_operator;
 
+/* OR-ed into operator_kind: skip the 1-norm series at construction.  The
+ * norms are then computed when the operator is first used (by
+ * qsw_expmv_series, or on the device by qsw_batch_series). */
+#define QSW_BUILD_DEFER_NORMS 0x100
+
 typedef struct qsw_ctx qsw_ctx;   /* device + stream + workspace cache */
 typedef struct qsw_op qsw_op;     /* one assembled superoperator L~ */
 
@@ -218,6 +223,88 @@ qsw_status qsw_expmv_series_host(qsw_op* op, const double* h_rho0, double t0, do
  * Re d_rho_series[c n + i (N~ + 1)] (Section 2.4; `gather_populations`). */
 qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t count,
                            double* d_pops);
+
+/* ------------------------------------------------------------ batching */
+
+/* Statistics of one qsw_batch_series call. */
+typedef struct {
+  int32_t walks;        /* walks in the batch */
+  int32_t clusters;     /* thread-block clusters (8 CTAs each) resident */
+  double norms_ms;      /* device time of the 1-norm phase */
+  double series_ms;     /* device time of the series phase */
+  int64_t matvecs;      /* applications of the walks' L~ to an n x n0 block */
+  int64_t fupdates;     /* sum over terms of the outputs updated */
+} qsw_batch_stats;
+
+/* Many independent walks in one launch (not in the paper): walk w is `ops[w]`
+ * (built with QSW_OPERATOR_MATRIX_FREE, any precision), evolved from the n0
+ * right-hand sides d_rho0[w] (n0 x n_w complex128, device, column c at offset
+ * 2 n_w c doubles; 1 <= n0 <= 4, treated as one n_w x n0 block as in
+ * Algorithm 3.2/5.2) over its own grid t0[w], dt[w], steps[w] (host arrays).
+ * d_pops[w] receives (steps[w]+1) x n0 x N~_w populations (device; entry
+ * [(k n0 + c) N~_w + i]).  Each walk is handled by one cluster of thread
+ * blocks; walks with Hermitian right-hand sides are computed on upper
+ * triangles.  The 1-norm estimates are computed on the device only when Code
+ * Fragment 3.1 needs them for the walk's time span.  At most 64 output times
+ * per Taylor block.  Synchronises the stream.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
+                            const double* const* d_rho0, int32_t n0, const double* t0,
+                            const double* dt, const int32_t* steps, double* const* d_pops,
+                            qsw_batch_stats* stats);
+
+/* ------------------------------------------------------------- serving */
+
+/* A request server (not in the paper): walks of any size, omega, time grid and
+ * precision are submitted from any host thread and evolved as they arrive.
+ * `workers` threads each own a CUDA stream; a free worker takes every queued
+ * request that fits the device-memory budget (oldest first, up to max_batch),
+ * builds their operators, runs them as one batched launch (qsw_batch_series,
+ * one thread-block cluster per walk) and copies the populations to the
+ * request's host buffer.  Requests arriving while batches run are launched by
+ * another worker on its own stream, so their work overlaps on the device.  A
+ * request's populations do not depend on which other requests share its
+ * batch.  memory_budget_bytes = 0 selects half of the free device memory; a
+ * request larger than the budget runs alone. */
+typedef struct {
+  int32_t workers;             /* concurrent batches (streams), >= 1; 0 -> 2 */
+  int32_t max_batch;           /* requests per batched launch; 0 -> 64 */
+  double memory_budget_bytes;  /* admission limit on the summed footprints */
+} qsw_server_config;
+
+typedef struct qsw_server qsw_server;
+
+typedef struct {
+  qsw_csr graph;               /* host digraph (copied at submit); H = Laplacian of G^u */
+  double omega;
+  int32_t precision;           /* qsw_precision */
+  const double* rho0;          /* host N x N complex128 column-major, or NULL */
+  const double* populations;   /* host N doubles (diagonal rho0), or NULL */
+  double t0, dt;
+  int32_t steps;
+  double* pops_out;            /* host (steps+1) x N doubles, written on completion;
+                                  must stay valid until qsw_server_wait returns */
+} qsw_request;
+
+typedef struct {
+  qsw_status status;
+  double latency_ms;           /* submit -> populations on the host */
+  double queue_ms;             /* submit -> taken by a worker */
+  char error[256];
+} qsw_request_result;
+
+qsw_status qsw_server_create(int device, const qsw_server_config* config, qsw_server** out);
+/* Enqueue a request; *id identifies it.  The graph and rho0 are copied. */
+qsw_status qsw_server_submit(qsw_server* server, const qsw_request* request, int64_t* id);
+/* Wait up to timeout_s seconds for request `id`; returns its status
+ * (QSW_ERR_NOT_CONVERGED on timeout, the request stays pending).  A completed
+ * request is forgotten after this call. */
+qsw_status qsw_server_wait(qsw_server* server, int64_t id, double timeout_s,
+                           qsw_request_result* result);
+qsw_status qsw_server_stats(qsw_server* server, int64_t* queued, int64_t* batches,
+                            double* bytes_in_use);
+/* Finish every queued request, stop the workers and free everything. */
+void qsw_server_destroy(qsw_server* server);
 
 /* ----------------------------------------------------- host-side helpers */
 

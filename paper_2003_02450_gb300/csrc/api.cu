@@ -40,7 +40,10 @@ qsw_status guarded(qsw_ctx* ctx, F&& f) {
   }
 }
 
-void set_device(const qsw_ctx* ctx) { QSW_CUDA_TRY(cudaSetDevice(ctx->device)); }
+void set_device(const qsw_ctx* ctx) {
+  QSW_CUDA_TRY(cudaSetDevice(ctx->device));
+  qsw::current_stream() = ctx->stream;
+}
 
 // Structural checks of a host CSR (see qsw.h conventions).
 void check_csr(const qsw_csr* m, const char* name, bool allow_diag) {
@@ -87,10 +90,11 @@ void check_ports(const qsw_port* p, int count, int N, const char* name) {
   }
 }
 
-void rebuild(Op& op) {
+void rebuild(Op& op, bool defer_norms) {
   qsw::build_jumps(op);
   qsw::prep_matfree(op);
   op.L = qsw::Csr{};
+  op.norms_ready = !defer_norms;
   if (op.opkind == QSW_OPERATOR_CSR) {
     qsw::Csr LH;
     qsw::assemble(op, false, op.L);
@@ -99,9 +103,15 @@ void rebuild(Op& op) {
     LH = qsw::Csr{};
     if (op.precision == QSW_C64_BULK) qsw::to_fp32(op, op.L);
     op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
-  } else {
+  } else if (!defer_norms) {
     qsw::compute_norms(op, nullptr, nullptr);
   }
+}
+
+void ensure_norms(Op& op) {
+  if (op.norms_ready) return;
+  qsw::compute_norms(op, nullptr, nullptr);
+  op.norms_ready = true;
 }
 
 }  // namespace
@@ -116,6 +126,12 @@ qsw_status qsw_create(qsw_ctx** out, int device, void* stream) {
     QSW_CUDA_TRY(cudaGetDeviceCount(&count));
     QSW_CHECK_ARG(device >= 0 && device < count, QSW_ERR_INVALID_ARG, "no such CUDA device");
     QSW_CUDA_TRY(cudaSetDevice(device));
+    // keep freed device memory in the pool (stream-ordered reuse, no OS round trips)
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+      unsigned long long keep = ~0ULL;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    }
     qsw_ctx* c = new qsw_ctx();
     c->device = device;
     c->stream = static_cast<cudaStream_t>(stream);
@@ -154,8 +170,12 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
                   "omega must lie in [0, 1]");
     QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
                   "unknown precision");
+    const bool defer = (operator_kind & QSW_BUILD_DEFER_NORMS) != 0;
+    operator_kind &= ~QSW_BUILD_DEFER_NORMS;
     QSW_CHECK_ARG(operator_kind == QSW_OPERATOR_MATRIX_FREE || operator_kind == QSW_OPERATOR_CSR,
                   QSW_ERR_INVALID_ARG, "unknown operator kind");
+    QSW_CHECK_ARG(!defer || operator_kind == QSW_OPERATOR_MATRIX_FREE, QSW_ERR_INVALID_ARG,
+                  "deferred norms need the matrix-free operator");
     if (H) {
       check_csr(H, "H", true);
       QSW_CHECK_ARG(H->n == G->n, QSW_ERR_INVALID_ARG, "H must be N x N");
@@ -199,7 +219,7 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
       op->snk_r.push_back(sinks[k].rate);
     }
     qsw::build_graph(*op);
-    rebuild(*op);
+    rebuild(*op, defer);
     *out = reinterpret_cast<qsw_op*>(op.release());
   });
 }
@@ -212,7 +232,7 @@ qsw_status qsw_set_omega(qsw_op* h, double omega) {
                   "omega must lie in [0, 1]");
     set_device(op->ctx);
     op->omega = omega;
-    rebuild(*op);
+    rebuild(*op, !op->norms_ready);
   });
 }
 
@@ -224,7 +244,10 @@ qsw_status qsw_op_info(const qsw_op* h, int64_t* n_tilde, int64_t* n, int64_t* n
     if (n_tilde) *n_tilde = op->Nt;
     if (n) *n = op->n;
     if (nnz) *nnz = op->nnz_csr;
-    if (norms9) memcpy(norms9, op->norms, sizeof(double) * qsw::kNormPowers);
+    if (norms9) {
+      ensure_norms(*const_cast<Op*>(op));
+      memcpy(norms9, op->norms, sizeof(double) * qsw::kNormPowers);
+    }
   });
 }
 
@@ -262,8 +285,8 @@ void qsw_op_destroy(qsw_op* h) {
   Op* op = reinterpret_cast<Op*>(h);
   if (!op) return;
   cudaSetDevice(op->ctx->device);
-  cudaStreamSynchronize(op->ctx->stream);
-  delete op;
+  qsw::current_stream() = op->ctx->stream;
+  delete op;   // buffers are released in stream order after the op's pending work
 }
 
 qsw_status qsw_initial_state(const qsw_op* h, const double* h_rho0, const double* h_pops,
@@ -326,6 +349,7 @@ qsw_status qsw_expmv_series(qsw_op* h, const double* d_rho0, double t0, double d
   return guarded(op ? op->ctx : nullptr, [&] {
     check_series_args(op, d_rho0, t0, dt, steps, d_out, d_pops);
     set_device(op->ctx);
+    ensure_norms(*op);
     qsw::run_series(*op, d_rho0, t0, dt, steps, d_out, d_pops, stats);
   });
 }
@@ -337,6 +361,7 @@ qsw_status qsw_expmv_series_host(qsw_op* h, const double* h_rho0, double t0, dou
   return guarded(op ? op->ctx : nullptr, [&] {
     check_series_args(op, h_rho0, t0, dt, steps, h_out, h_pops);
     set_device(op->ctx);
+    ensure_norms(*op);
     cudaStream_t st = op->ctx->stream;
     qsw::DevBuf rho0, out, pops;
     rho0.alloc(sizeof(double2) * op->n);
@@ -366,6 +391,26 @@ qsw_status qsw_populations(const qsw_op* h, const double* d_rho, int32_t count, 
 }
 
 int64_t qsw_kernel_launches(void) { return qsw::g_launches.load(); }
+
+qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
+                            const double* const* d_rho0, int32_t n0, const double* t0,
+                            const double* dt, const int32_t* steps, double* const* d_pops,
+                            qsw_batch_stats* stats) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx && count >= 1 && ops && d_rho0 && t0 && dt && steps && d_pops,
+                  QSW_ERR_INVALID_ARG, "bad arguments to qsw_batch_series");
+    for (int w = 0; w < count; ++w) {
+      QSW_CHECK_ARG(ops[w] && d_rho0[w] && d_pops[w], QSW_ERR_INVALID_ARG, "NULL walk pointer");
+      QSW_CHECK_ARG(reinterpret_cast<Op*>(ops[w])->ctx == ctx, QSW_ERR_INVALID_ARG,
+                    "operator from another context");
+      check_series_args(reinterpret_cast<Op*>(ops[w]), d_rho0[w], t0[w], dt[w], steps[w], nullptr,
+                        d_pops[w]);
+    }
+    set_device(ctx);
+    qsw::run_batch(ctx, count, reinterpret_cast<Op* const*>(ops), d_rho0, n0, t0, dt, steps,
+                   d_pops, stats);
+  });
+}
 
 qsw_status qsw_theta_table(int32_t precision, double* theta55) {
   return guarded(nullptr, [&] {

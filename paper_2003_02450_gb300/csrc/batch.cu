@@ -1,0 +1,808 @@
+// Batched L-QSW series: many independent walks of uneven size in one launch.
+//
+// Each walk is handled by one thread-block cluster of kCl CTAs; clusters take
+// walks from a queue ordered by decreasing size (largest first), so big and
+// small walks pack onto the GPU together.  Inside a cluster every pass over the
+// walk's elements is split over the cluster's warps, and passes are separated
+// by hardware cluster barriers (barrier.cluster: no spin loop).  Reductions go
+// through distributed shared memory: each CTA reduces its part, then every CTA
+// reads the kCl partials in rank order, so all CTAs hold the same value and
+// take the same decisions.
+//
+// Phase 1 (norms): the exact ||L||_1 and, only when Code Fragment 3.1 needs
+// them for the walk's time span (condition (3.13) fails), the Higham--Tisseur
+// estimates of ||L^p||_1, p = 2..9 -- the same algorithm as norms.cu, with its
+// branches taken on the device.
+// Phase 2 (series): the walk's plan (params.cuh) and its Taylor blocks on a
+// block of n0 <= 4 right-hand sides (A-H treat B = [b_1 .. b_n0] as one matrix:
+// ||B||_inf is the largest row sum of moduli), populations of every output.
+// Hermitian right-hand sides are computed on upper triangles as in series.cu.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+
+#include "matfree.cuh"
+#include "op.h"
+#include "params.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace qsw {
+
+// theta tables for this translation unit (uploaded with the series tables)
+__constant__ double c_theta_b[2][kMMax];
+
+void upload_theta_batch() {
+  QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta_b, theta_table(QSW_C128), sizeof(double) * kMMax, 0));
+  QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta_b, theta_table(QSW_C64_BULK), sizeof(double) * kMMax,
+                                  sizeof(double) * kMMax));
+}
+
+namespace {
+
+constexpr int kCl = 8;        // CTAs per cluster
+constexpr int kBT = 256;      // threads per CTA
+constexpr int kBW = kBT / 32;
+constexpr int kMaxRhs = 4;
+constexpr int kItMax = 5;
+constexpr int kMaxHist = 2 * (kItMax + 1);
+constexpr int kBDMax = 64;    // outputs per Taylor block in the batched kernel
+constexpr unsigned long long kSeed = 0x51535700ULL;
+
+struct BWalk {
+  MfOp<double> mf64;   // L
+  MfOp<double> mfh64;  // L^H
+  MfOp<float> mf32;    // L, FP32 coefficients
+  int Nt;
+  long long n;
+  int n0;
+  int f32;             // complex64 bulk
+  int herm;            // every right-hand side Hermitian
+  const double2* rho0; // n0 x n
+  double* pops;        // (steps+1) x n0 x Nt
+  double t0, dt;
+  int steps;
+  double norm_span;    // max(t0, steps dt): decides whether estimates are needed
+  // phase 1 outputs / phase 2 inputs
+  double* dp;          // [kNormPowers + 1]
+  double2* est;        // phase 1 workspace: X, Y, W (2 n each), h (n doubles)
+  // phase 2 workspace
+  void* kbuf;          // 2 x n0 x n of VT
+  double2* fring;      // ring x n0 x n
+  int ring;
+  Job* jobs;
+  int njobs;
+  long long* counters; // [0] matvecs, [1] fupdates, [2] plan mismatch
+};
+
+struct BArgs {
+  BWalk* walks;
+  const int* order;    // walk indices, largest first
+  int count;
+  unsigned int* queue; // [0] phase-1 counter, [1] phase-2 counter
+  double tol[2];
+};
+
+__device__ __forceinline__ unsigned long long bits_of(double v) {
+  return (unsigned long long)__double_as_longlong(v);
+}
+__device__ __forceinline__ double of_bits(unsigned long long b) {
+  return __longlong_as_double((long long)b);
+}
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
+                                                         unsigned long long i) {
+  unsigned long long z = seed + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  return z ^ (z >> 31);
+}
+
+// --------------------------------------------------------- cluster reductions
+struct Red {
+  double v[kBW][2];
+  int idx[kBW][2];
+  double blk[2];
+  int blki[2];
+  double out[2];
+  int outi[2];
+};
+
+__device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
+  if (ib < 0) return ia >= 0;
+  if (ia < 0) return false;
+  return va > vb || (va == vb && ia < ib);
+}
+
+// Sum of (a, b) over the cluster, fixed order (deterministic).
+__device__ void cl_sum2(cg::cluster_group& cl, Red& R, double a, double b, double& oa, double& ob) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) { R.v[warp][0] = a; R.v[warp][1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int w = 0; w < kBW; ++w) { s0 += R.v[w][0]; s1 += R.v[w][1]; }
+    R.blk[0] = s0;
+    R.blk[1] = s1;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int r = 0; r < kCl; ++r) {
+      const Red* p = cl.map_shared_rank(&R, r);
+      s0 += p->blk[0];
+      s1 += p->blk[1];
+    }
+    R.out[0] = s0;
+    R.out[1] = s1;
+  }
+  cl.sync();
+  oa = R.out[0];
+  ob = R.out[1];
+}
+
+// Max of two non-negative values over the cluster.
+__device__ void cl_max2(cg::cluster_group& cl, Red& R, double a, double b, double& oa, double& ob) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+  }
+  if (lane == 0) { R.v[warp][0] = a; R.v[warp][1] = b; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int w = 0; w < kBW; ++w) { s0 = fmax(s0, R.v[w][0]); s1 = fmax(s1, R.v[w][1]); }
+    R.blk[0] = s0;
+    R.blk[1] = s1;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    double s0 = 0, s1 = 0;
+    for (int r = 0; r < kCl; ++r) {
+      const Red* p = cl.map_shared_rank(&R, r);
+      s0 = fmax(s0, p->blk[0]);
+      s1 = fmax(s1, p->blk[1]);
+    }
+    R.out[0] = s0;
+    R.out[1] = s1;
+  }
+  cl.sync();
+  oa = R.out[0];
+  ob = R.out[1];
+}
+
+// argmax over the cluster: larger value first, ties to the smaller index.
+__device__ void cl_argmax(cg::cluster_group& cl, Red& R, double v, int i, double& ov, int& oi) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const int i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    if (better(v2, i2, v, i)) { v = v2; i = i2; }
+  }
+  if (lane == 0) { R.v[warp][0] = v; R.idx[warp][0] = i; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double bv = 0;
+    int bi = -1;
+    for (int w = 0; w < kBW; ++w)
+      if (better(R.v[w][0], R.idx[w][0], bv, bi)) { bv = R.v[w][0]; bi = R.idx[w][0]; }
+    R.blk[0] = bv;
+    R.blki[0] = bi;
+  }
+  cl.sync();
+  if (threadIdx.x == 0) {
+    double bv = 0;
+    int bi = -1;
+    for (int r = 0; r < kCl; ++r) {
+      const Red* p = cl.map_shared_rank(&R, r);
+      if (better(p->blk[0], p->blki[0], bv, bi)) { bv = p->blk[0]; bi = p->blki[0]; }
+    }
+    R.out[0] = bv;
+    R.outi[0] = bi;
+  }
+  cl.sync();
+  ov = R.out[0];
+  oi = R.outi[0];
+}
+
+// Next walk from the queue (cluster rank 0 takes it, everyone reads it).
+__device__ int next_walk(cg::cluster_group& cl, unsigned int* counter, int* s_w, const BArgs& a) {
+  if (cl.block_rank() == 0 && threadIdx.x == 0) {
+    const unsigned k = atomicAdd(counter, 1u);
+    *s_w = k < (unsigned)a.count ? a.order[k] : -1;
+  }
+  cl.sync();
+  const int w = *cl.map_shared_rank(s_w, 0);
+  cl.sync();
+  return w;
+}
+
+// y_c = scale * M x_c for `cols` vectors (general elements), FP64, over the
+// cluster's warps; M = L or L^H.
+template <bool ADJ>
+__device__ void cl_apply64(const MfOp<double>& op, int cols, const double2* x, double2* y,
+                           long long n) {
+  const int gw = (int)(cg::this_cluster().block_rank() * kBW + (threadIdx.x >> 5));
+  const int lane = threadIdx.x & 31;
+  const long long nitems = mf_item_count(op.Nt, false);
+  for (long long k = gw; k < nitems; k += kCl * kBW) {
+    int j, i0;
+    mf_item(k, op.Nt, false, j, i0);
+    int irow[2];
+    for (int u = 0; u < 2; ++u) {
+      const int i = i0 + lane + 32 * u;
+      irow[u] = i < op.Nt ? i : -1;
+    }
+    for (int c = 0; c < cols; ++c) {
+      const double2* xc = x + c * n;
+      double cx[2], cy[2];
+      mf_partB<double, double2, 2>(op, xc, j, irow, cx, cy);
+      for (int u = 0; u < 2; ++u) {
+        if (irow[u] < 0) continue;
+        double yx, yy;
+        mf_finish<double, double2, ADJ>(op, xc, irow[u], j, cx[u], cy[u], yx, yy);
+        y[c * n + irow[u] + (long long)op.Nt * j] = make_double2(yx, yy);
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- phase 1
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
+batch_norms_kernel(BArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ Red R;
+  __shared__ int s_w;
+  const int crank = (int)cl.block_rank();
+  const long long ct = (long long)crank * kBT + threadIdx.x;   // thread index in the cluster
+  const long long cstride = (long long)kCl * kBT;
+  for (;;) {
+    const int wi = next_walk(cl, &a.queue[0], &s_w, a);
+    if (wi < 0) break;
+    BWalk& W = a.walks[wi];
+    const int Nt = W.Nt;
+    const long long n = W.n;
+    const MfOp<double>& L = W.mf64;
+    // exact ||L||_1: column (i, j) sums |c| over H rows i and j, |D_ij|, and
+    // the rates leaving i when i = j (= dtot_i = -2 ad_i)
+    double best = 0.0;
+    for (long long r = ct; r < n; r += cstride) {
+      const int i = (int)(r % Nt), j = (int)(r / Nt);
+      double s = 0.0;
+      if (i < L.N) for (int e = L.hrow[i]; e < L.hrow[i + 1]; ++e) s += fabs(L.hval[e]);
+      if (j < L.N) for (int e = L.hrow[j]; e < L.hrow[j + 1]; ++e) s += fabs(L.hval[e]);
+      s += hypot(L.ad[i] + L.ad[j], L.hw[j] - L.hw[i]);
+      if (i == j) s += -2.0 * L.ad[i];
+      best = fmax(best, s);
+    }
+    double one, dummy;
+    cl_max2(cl, R, best, 0.0, one, dummy);
+    double norms[kNormPowers] = {0};
+    norms[0] = one;
+    const int prec = W.f32 ? 1 : 0;
+    const bool need = one > 0.0 &&
+                      !small_norm_condition(W.norm_span * one, c_theta_b[prec], W.n0);
+    if (need) {
+      // Higham--Tisseur Algorithm 2.4 for A^p, p = 2..9 (t = 2 columns)
+      double2* X = W.est;
+      double2* Y = X + 2 * n;
+      double2* Wb = Y + 2 * n;
+      double* h = reinterpret_cast<double*>(Wb + 2 * n);
+      const int t = n >= 2 ? 2 : 1;
+      for (int p = 2; p <= kNormPowers; ++p) {
+        // X = [1, +-1] / n
+        for (long long r = ct; r < n; r += cstride) {
+          X[r] = make_double2(1.0 / n, 0.0);
+          if (t > 1) {
+            const bool neg = (splitmix64(kSeed, (unsigned long long)r) >> 63) != 0;
+            X[n + r] = make_double2(neg ? -1.0 / n : 1.0 / n, 0.0);
+          }
+        }
+        cl.sync();
+        int hist[kMaxHist];
+        int nhist = 0;
+        double est_old = 0.0, est = 0.0;
+        int ind[2] = {0, 0};
+        int ind_best = 0;
+        for (int k = 1;; ++k) {
+          // Y = A^p X (ping-pong through Wb)
+          const double2* src = X;
+          for (int q = 0; q < p; ++q) {
+            double2* dst = ((p - q) % 2 == 1) ? Y : Wb;
+            cl_apply64<false>(L, t, src, dst, n);
+            cl.sync();
+            src = dst;
+          }
+          double c0 = 0, c1 = 0;
+          for (long long r = ct; r < n; r += cstride) {
+            const double2 y0 = __ldcg(Y + r);
+            c0 += hypot(y0.x, y0.y);
+            if (t > 1) {
+              const double2 y1 = __ldcg(Y + n + r);
+              c1 += hypot(y1.x, y1.y);
+            }
+          }
+          double cn0, cn1;
+          cl_sum2(cl, R, c0, c1, cn0, cn1);
+          const int jbest = (t > 1 && cn1 > cn0) ? 1 : 0;
+          est = jbest ? cn1 : cn0;
+          if (est > est_old || k == 2) ind_best = ind[jbest];
+          if (k >= 2 && est <= est_old) { est = est_old; break; }
+          est_old = est;
+          if (k > kItMax) break;
+          // S = sign(Y) into X, Z = (A^H)^p S into Y
+          for (long long r = ct; r < (long long)t * n; r += cstride) {
+            const double2 y = __ldcg(Y + r);
+            const double m = hypot(y.x, y.y);
+            X[r] = m == 0.0 ? make_double2(1.0, 0.0) : make_double2(y.x / m, y.y / m);
+          }
+          cl.sync();
+          src = X;
+          for (int q = 0; q < p; ++q) {
+            double2* dst = ((p - q) % 2 == 1) ? Y : Wb;
+            cl_apply64<true>(W.mfh64, t, src, dst, n);
+            cl.sync();
+            src = dst;
+          }
+          // h_i = max_c |Z_ic|, argmax (ties to the smaller index)
+          double bv = 0;
+          int bi = -1;
+          for (long long r = ct; r < n; r += cstride) {
+            const double2 z0 = __ldcg(Y + r);
+            double v = hypot(z0.x, z0.y);
+            if (t > 1) {
+              const double2 z1 = __ldcg(Y + n + r);
+              v = fmax(v, hypot(z1.x, z1.y));
+            }
+            h[r] = v;
+            if (better(v, (int)r, bv, bi)) { bv = v; bi = (int)r; }
+          }
+          double hmax;
+          int imax;
+          cl_argmax(cl, R, bv, bi, hmax, imax);   // (syncs make h visible)
+          if (k >= 2 && hmax == __ldcg(h + ind_best)) break;
+          // top-2 overall, then the first t indices not used before
+          auto argmax_excl = [&](const int* ex, int nex, double& ov, int& oi) {
+            double v2 = 0;
+            int i2 = -1;
+            for (long long r = ct; r < n; r += cstride) {
+              bool skip = false;
+              for (int q = 0; q < nex; ++q) skip |= ex[q] == (int)r;
+              if (skip) continue;
+              if (better(h[r], (int)r, v2, i2)) { v2 = h[r]; i2 = (int)r; }
+            }
+            cl_argmax(cl, R, v2, i2, ov, oi);
+          };
+          int fresh[2] = {imax, -1};
+          if (t > 1) {
+            double v2;
+            int i2;
+            argmax_excl(&imax, 1, v2, i2);
+            bool in0 = false, in1 = false;
+            for (int q = 0; q < nhist; ++q) { in0 |= hist[q] == imax; in1 |= hist[q] == i2; }
+            if (in0 && in1) break;
+            int ex[kMaxHist + 1];
+            for (int q = 0; q < nhist; ++q) ex[q] = hist[q];
+            double fv;
+            argmax_excl(ex, nhist, fv, fresh[0]);
+            ex[nhist] = fresh[0];
+            argmax_excl(ex, nhist + 1, fv, fresh[1]);
+            if (fresh[0] < 0 || fresh[1] < 0) break;
+          }
+          ind[0] = fresh[0];
+          ind[1] = fresh[1];
+          for (long long r = ct; r < (long long)t * n; r += cstride) X[r] = make_double2(0.0, 0.0);
+          cl.sync();
+          if (crank == 0 && threadIdx.x == 0) {
+            X[ind[0]] = make_double2(1.0, 0.0);
+            if (t > 1) X[n + ind[1]] = make_double2(1.0, 0.0);
+          }
+          cl.sync();
+          if (nhist + t <= kMaxHist) {
+            hist[nhist++] = ind[0];
+            if (t > 1) hist[nhist++] = ind[1];
+          }
+        }
+        norms[p - 1] = est;
+      }
+    }
+    if (crank == 0 && threadIdx.x == 0) {
+      W.dp[0] = norms[0];
+      for (int p = 2; p <= kNormPowers; ++p) W.dp[p - 1] = need ? pow(norms[p - 1], 1.0 / p) : 0.0;
+      W.dp[kNormPowers] = 0.0;
+    }
+    cl.sync();
+  }
+}
+
+// --------------------------------------------------------------- phase 2
+template <class VT> struct BC;
+template <> struct BC<double2> {
+  using R = double;
+  __device__ static double2 mk(double a, double b) { return make_double2(a, b); }
+  __device__ static const MfOp<double>& mf(const BWalk& w) { return w.mf64; }
+};
+template <> struct BC<float2> {
+  using R = float;
+  __device__ static float2 mk(float a, float b) { return make_float2(a, b); }
+  __device__ static const MfOp<float>& mf(const BWalk& w) { return w.mf32; }
+};
+
+template <class VT>
+__device__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double tol, double* s_coef,
+                         double* s_step, double* s_c1, int* s_active) {
+  using Rt = typename BC<VT>::R;
+  const int crank = (int)cl.block_rank();
+  const long long ct = (long long)crank * kBT + threadIdx.x;
+  const long long cstride = (long long)kCl * kBT;
+  const int Nt = W.Nt;
+  const long long n = W.n;
+  const int n0 = W.n0;
+  const bool herm = W.herm != 0;
+  const MfOp<Rt>& op = BC<VT>::mf(W);
+  VT* kcur = static_cast<VT*>(W.kbuf);
+  VT* knext = kcur + (long long)n0 * n;
+  const int lane = threadIdx.x & 31;
+  const int gw = crank * kBW + (threadIdx.x >> 5);
+  auto fslot = [&](int idx) { return W.fring + (long long)(idx % W.ring) * n0 * n; };
+  long long matvecs = 0, fupd = 0;
+
+  for (int jb = 0; jb < W.njobs; ++jb) {
+    const Job J = W.jobs[jb];
+    const double2* Z = J.z_slot < 0 ? W.rho0 : fslot(J.z_slot);
+    VT* kc = static_cast<VT*>(W.kbuf);
+    VT* kn = kc + (long long)n0 * n;
+    // init: Khat_0 = Z, F_k = Z, ||Z||_inf
+    double zn = 0.0;
+    for (long long r = ct; r < n; r += cstride) {
+      const int i = (int)(r % Nt), j = (int)(r / Nt);
+      double rs = 0.0;
+      for (int c = 0; c < n0; ++c) {
+        double2 z;
+        if (herm && i > j) {
+          z = __ldcg(Z + c * n + j + (long long)Nt * i);
+          z.y = -z.y;
+        } else {
+          z = __ldcg(Z + c * n + r);
+        }
+        kc[c * n + r] = BC<VT>::mk((Rt)z.x, (Rt)z.y);
+        for (int k = 0; k < J.d; ++k) fslot(J.out_index0 + k)[c * n + r] = z;
+        rs += n0 == 1 ? z.x * z.x + z.y * z.y : hypot(z.x, z.y);
+      }
+      zn = fmax(zn, rs);
+    }
+    double znorm, dmy;
+    cl_max2(cl, R, zn, 0.0, znorm, dmy);
+    if (n0 == 1) znorm = sqrt(znorm);
+    for (int k = threadIdx.x; k < J.d; k += kBT) {
+      s_c1[k] = znorm;
+      s_coef[k] = 1.0;
+      s_step[k] = (double)(k + 1) / J.d;
+      s_active[k] = 1;
+    }
+    __syncthreads();
+    for (int p = 1; p <= J.m; ++p) {
+      const Rt scale = (Rt)(J.hspan / p);
+      for (int k = threadIdx.x; k < J.d; k += kBT) s_coef[k] *= s_step[k];
+      __syncthreads();
+      double kmax = 0.0;
+      double fmx[kBDMax > 8 ? 8 : kBDMax];
+      for (int u = 0; u < 8; ++u) fmx[u] = 0.0;
+      double fmx_rest = 0.0;   // outputs k >= 8 are folded (only their max matters per k below)
+      const long long nitems = mf_item_count(Nt, herm);
+      for (long long it = gw; it < nitems; it += kCl * kBW) {
+        int j, i0;
+        mf_item(it, Nt, herm, j, i0);
+        int irow[2];
+        for (int u = 0; u < 2; ++u) {
+          const int i = i0 + lane + 32 * u;
+          irow[u] = (i < Nt && (!herm || i <= j)) ? i : -1;
+        }
+        Rt yx[2][kMaxRhs], yy[2][kMaxRhs];
+        for (int c = 0; c < n0; ++c) {
+          Rt cx[2], cy[2];
+          mf_partB<Rt, VT, 2>(op, kc + c * n, j, irow, cx, cy);
+          for (int u = 0; u < 2; ++u) {
+            if (irow[u] < 0) continue;
+            mf_finish<Rt, VT, false>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c], yy[u][c]);
+          }
+        }
+        for (int u = 0; u < 2; ++u) {
+          if (irow[u] < 0) continue;
+          const int i = irow[u];
+          const long long r = i + (long long)Nt * j;
+          double rs = 0.0;
+          for (int c = 0; c < n0; ++c) {
+            const Rt ax = yx[u][c] * scale, ay = yy[u][c] * scale;
+            kn[c * n + r] = BC<VT>::mk(ax, ay);
+            if (herm && i != j) kn[c * n + j + (long long)Nt * i] = BC<VT>::mk(ax, -ay);
+            yx[u][c] = ax;
+            yy[u][c] = ay;
+            rs += n0 == 1 ? (double)ax * ax + (double)ay * ay
+                          : (double)sqrtf((float)ax * (float)ax + (float)ay * (float)ay);
+          }
+          kmax = fmax(kmax, rs);
+          for (int k = 0; k < J.d; ++k) {
+            if (!s_active[k]) continue;
+            double2* F = fslot(J.out_index0 + k);
+            double fs = 0.0;
+            for (int c = 0; c < n0; ++c) {
+              double2 f = __ldcg(F + c * n + r);
+              f.x = fma(s_coef[k], (double)yx[u][c], f.x);
+              f.y = fma(s_coef[k], (double)yy[u][c], f.y);
+              F[c * n + r] = f;
+              fs += n0 == 1 ? f.x * f.x + f.y * f.y
+                            : (double)sqrtf((float)f.x * (float)f.x + (float)f.y * (float)f.y);
+            }
+            if (k < 8) fmx[k] = fmax(fmx[k], fs);
+            else atomicMax(reinterpret_cast<unsigned long long*>(&s_c1[kBDMax + k]), bits_of(fs));
+          }
+        }
+      }
+      (void)fmx_rest;
+      // norms: K and the first outputs through cl_max2 pairs
+      double gk, g0;
+      cl_max2(cl, R, kmax, fmx[0], gk, g0);
+      double fn[kBDMax];
+      fn[0] = g0;
+      for (int k = 1; k < J.d && k < 8; k += 2) {
+        double a0, a1;
+        cl_max2(cl, R, fmx[k], k + 1 < 8 ? fmx[k + 1] : 0.0, a0, a1);
+        fn[k] = a0;
+        if (k + 1 < J.d && k + 1 < 8) fn[k + 1] = a1;
+      }
+      for (int k = 8; k < J.d; ++k) {
+        double a0, a1;
+        cl_max2(cl, R, of_bits(*reinterpret_cast<unsigned long long*>(&s_c1[kBDMax + k])), 0.0,
+                a0, a1);
+        fn[k] = a0;
+        __syncthreads();
+        if (threadIdx.x == 0) s_c1[kBDMax + k] = 0.0;
+      }
+      ++matvecs;
+      for (int k = 0; k < J.d; ++k) fupd += s_active[k];
+      const double normk = n0 == 1 ? sqrt(gk) : gk;
+      int any = 0;
+      for (int k = 0; k < J.d; ++k) {
+        if (!s_active[k]) continue;
+        const double c2 = s_coef[k] * normk;
+        const double nf = n0 == 1 ? sqrt(fn[k]) : fn[k];
+        const bool stop = s_c1[k] + c2 <= tol * nf;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          if (stop) s_active[k] = 0;
+          s_c1[k] = c2;
+        }
+        __syncthreads();
+        any |= !stop;
+      }
+      VT* t = kc;
+      kc = kn;
+      kn = t;
+      if (!any) break;
+    }
+    // populations of the finished outputs
+    if (J.final_outputs && W.pops) {
+      const long long tot = (long long)J.d * n0 * Nt;
+      for (long long q = ct; q < tot; q += cstride) {
+        const int k = (int)(q / ((long long)n0 * Nt));
+        const int rem = (int)(q % ((long long)n0 * Nt));
+        const int c = rem / Nt, v = rem % Nt;
+        const double2 z = __ldcg(fslot(J.out_index0 + k) + c * n + (long long)v * (Nt + 1));
+        W.pops[((long long)(J.out_index0 + k) * n0 + c) * Nt + v] = z.x;
+      }
+    }
+    cl.sync();   // outputs complete before the next block reads them
+  }
+  if (crank == 0 && threadIdx.x == 0) {
+    W.counters[0] = matvecs;
+    W.counters[1] = fupd;
+  }
+  (void)kcur;
+  (void)knext;
+}
+
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
+batch_series_kernel(BArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ Red R;
+  __shared__ int s_w;
+  __shared__ double s_coef[kBDMax];
+  __shared__ double s_step[kBDMax];
+  __shared__ double s_c1[2 * kBDMax];
+  __shared__ int s_active[kBDMax];
+  for (int k = threadIdx.x; k < 2 * kBDMax; k += kBT) s_c1[k] = 0.0;
+  __syncthreads();
+  for (;;) {
+    const int wi = next_walk(cl, &a.queue[1], &s_w, a);
+    if (wi < 0) break;
+    BWalk& W = a.walks[wi];
+    // plan on the device from the walk's own norms
+    if (cl.block_rank() == 0 && threadIdx.x == 0) {
+      const PlanInfo info = plan_series(W.dp, c_theta_b[W.f32 ? 1 : 0], W.t0, W.dt, W.steps, W.n0,
+                                        W.ring, W.jobs, W.njobs);
+      if (info.njobs != W.njobs || info.max_d > kBDMax) W.counters[2] = 1;
+    }
+    cl.sync();
+    if (__ldcg(&W.counters[2])) continue;   // L2 read: every CTA sees rank 0's flag
+    if (W.f32) run_walk<float2>(cl, R, W, a.tol[1], s_coef, s_step, s_c1, s_active);
+    else run_walk<double2>(cl, R, W, a.tol[0], s_coef, s_step, s_c1, s_active);
+  }
+}
+
+__global__ void herm_check_many(int Nt, long long n, int cols, const double2* __restrict__ x,
+                                unsigned long long* __restrict__ out) {
+  unsigned long long da = 0, xa = 0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n * cols;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = q / n, r = q % n;
+    const int i = (int)(r % Nt), j = (int)(r / Nt);
+    const double2 u = x[c * n + r];
+    const double2 v = x[c * n + j + (long long)Nt * i];
+    const double ex = u.x - v.x, ey = u.y + v.y;
+    da = max(da, bits_of(ex * ex + ey * ey));
+    xa = max(xa, bits_of(u.x * u.x + u.y * u.y));
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    da = max(da, __shfl_xor_sync(0xffffffffu, da, o));
+    xa = max(xa, __shfl_xor_sync(0xffffffffu, xa, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&out[0], da);
+    atomicMax(&out[1], xa);
+  }
+}
+
+}  // namespace
+
+void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
+               const double* t0s, const double* dts, const int* steps, double* const* d_pops,
+               qsw_batch_stats* stats) {
+  cudaStream_t st = ctx->stream;
+  QSW_CHECK_ARG(n0 >= 1 && n0 <= kMaxRhs, QSW_ERR_INVALID_ARG, "n0 must be 1..4");
+  std::vector<BWalk> hw(count);
+  std::vector<DevBuf> bufs;
+  bufs.reserve(4 * count + 4);
+  // Hermitian check of every walk's right-hand sides (one readback)
+  DevBuf hb;
+  hb.alloc(sizeof(unsigned long long) * 2 * count);
+  QSW_CUDA_TRY(cudaMemsetAsync(hb.p, 0, hb.bytes, st));
+  for (int w = 0; w < count; ++w) {
+    const Op& op = *ops[w];
+    QSW_CHECK_ARG(op.opkind == QSW_OPERATOR_MATRIX_FREE, QSW_ERR_INVALID_ARG,
+                  "batched series needs matrix-free operators");
+    QSW_LAUNCH herm_check_many<<<grid_for(op.n * n0, 256, 1024), 256, 0, st>>>(
+        op.Nt, op.n, n0, reinterpret_cast<const double2*>(d_rho0[w]),
+        hb.as<unsigned long long>() + 2 * w);
+  }
+  QSW_CUDA_TRY(cudaGetLastError());
+  std::vector<unsigned long long> hbits(2 * count);
+  QSW_CUDA_TRY(cudaMemcpyAsync(hbits.data(), hb.p, hb.bytes, cudaMemcpyDeviceToHost, st));
+  // per-walk descriptors, phase-1 workspace
+  DevBuf dpbuf, cnt;
+  dpbuf.alloc(sizeof(double) * (kNormPowers + 1) * count);
+  cnt.alloc(sizeof(long long) * 4 * count);
+  QSW_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, cnt.bytes, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int w = 0; w < count; ++w) {
+    const Op& op = *ops[w];
+    BWalk& W = hw[w];
+    memset(&W, 0, sizeof(W));
+    W.mf64 = make_mf<double>(op, false);
+    W.mfh64 = make_mf<double>(op, true);
+    W.mf32 = make_mf<float>(op, false);
+    W.Nt = op.Nt;
+    W.n = op.n;
+    W.n0 = n0;
+    W.f32 = op.precision == QSW_C64_BULK;
+    double a2, m2;
+    memcpy(&a2, &hbits[2 * w], 8);
+    memcpy(&m2, &hbits[2 * w + 1], 8);
+    W.herm = sqrt(a2) <= 1e-13 * std::max(1.0, sqrt(m2));
+    W.rho0 = reinterpret_cast<const double2*>(d_rho0[w]);
+    W.pops = d_pops[w];
+    W.t0 = t0s[w];
+    W.dt = dts[w];
+    W.steps = steps[w];
+    W.norm_span = std::max(t0s[w], steps[w] * dts[w]);
+    W.dp = dpbuf.as<double>() + (kNormPowers + 1) * w;
+    W.counters = cnt.as<long long>() + 4 * w;
+    bufs.emplace_back();
+    bufs.back().alloc(sizeof(double2) * 6 * op.n + sizeof(double) * op.n);
+    W.est = bufs.back().as<double2>();
+  }
+  std::vector<int> order(count);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hw[x].n > hw[y].n; });
+  DevBuf dwalks, dorder, dq;
+  dwalks.alloc(sizeof(BWalk) * count);
+  dorder.alloc(sizeof(int) * count);
+  dq.alloc(sizeof(unsigned) * 2);
+  QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice, st));
+  QSW_CUDA_TRY(cudaMemcpyAsync(dorder.p, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
+  QSW_CUDA_TRY(cudaMemsetAsync(dq.p, 0, sizeof(unsigned) * 2, st));
+  BArgs args{};
+  args.walks = dwalks.as<BWalk>();
+  args.order = dorder.as<int>();
+  args.count = count;
+  args.queue = dq.as<unsigned>();
+  args.tol[0] = tolerance(QSW_C128);
+  args.tol[1] = tolerance(QSW_C64_BULK);
+  int max_clusters = 0;
+  {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCl * 4096);
+    cfg.blockDim = dim3(kBT);
+    cfg.numAttrs = 0;   // the kernel declares its cluster shape
+    QSW_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, batch_series_kernel, &cfg));
+  }
+  const int clusters = std::max(1, std::min(max_clusters, count));
+  cudaEvent_t e0, e1, e2;
+  QSW_CUDA_TRY(cudaEventCreate(&e0));
+  QSW_CUDA_TRY(cudaEventCreate(&e1));
+  QSW_CUDA_TRY(cudaEventCreate(&e2));
+  QSW_CUDA_TRY(cudaEventRecord(e0, st));
+  QSW_LAUNCH batch_norms_kernel<<<clusters * kCl, kBT, 0, st>>>(args);
+  QSW_CUDA_TRY(cudaGetLastError());
+  QSW_CUDA_TRY(cudaEventRecord(e1, st));
+  // plans (host copy, same code as the device) size the phase-2 workspace
+  std::vector<double> dps((kNormPowers + 1) * count);
+  QSW_CUDA_TRY(cudaMemcpyAsync(dps.data(), dpbuf.p, sizeof(double) * dps.size(),
+                               cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int w = 0; w < count; ++w) {
+    BWalk& W = hw[w];
+    const double* theta = theta_table(W.f32 ? QSW_C64_BULK : QSW_C128);
+    const PlanInfo info = plan_series(&dps[(kNormPowers + 1) * w], theta, W.t0, W.dt, W.steps,
+                                      n0, 0, nullptr, 0);
+    QSW_CHECK_ARG(info.max_d <= kBDMax, QSW_ERR_INVALID_ARG,
+                  "batched series: more than 64 outputs per Taylor block");
+    W.njobs = info.njobs;
+    W.ring = info.max_d + 1;
+    const size_t vb = W.f32 ? sizeof(float2) : sizeof(double2);
+    bufs.emplace_back();
+    bufs.back().alloc(2 * vb * n0 * (size_t)W.n);
+    W.kbuf = bufs.back().p;
+    bufs.emplace_back();
+    bufs.back().alloc(sizeof(double2) * (size_t)W.ring * n0 * W.n);
+    W.fring = bufs.back().as<double2>();
+    bufs.emplace_back();
+    bufs.back().alloc(sizeof(Job) * std::max(1, W.njobs));
+    W.jobs = bufs.back().as<Job>();
+  }
+  QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice, st));
+  QSW_LAUNCH batch_series_kernel<<<clusters * kCl, kBT, 0, st>>>(args);
+  QSW_CUDA_TRY(cudaGetLastError());
+  QSW_CUDA_TRY(cudaEventRecord(e2, st));
+  std::vector<long long> hc(4 * count);
+  QSW_CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt.p, cnt.bytes, cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms1 = 0, ms2 = 0;
+  cudaEventElapsedTime(&ms1, e0, e1);
+  cudaEventElapsedTime(&ms2, e1, e2);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(e2);
+  for (int w = 0; w < count; ++w)
+    QSW_CHECK_ARG(hc[4 * w + 2] == 0, QSW_ERR_CUDA, "batched series: device plan mismatch");
+  if (stats) {
+    stats->walks = count;
+    stats->clusters = clusters;
+    stats->norms_ms = ms1;
+    stats->series_ms = ms2;
+    long long mv = 0, fu = 0;
+    for (int w = 0; w < count; ++w) { mv += hc[4 * w]; fu += hc[4 * w + 1]; }
+    stats->matvecs = mv;
+    stats->fupdates = fu;
+  }
+}
+
+}  // namespace qsw

@@ -71,6 +71,7 @@ struct Op {
   double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
   DevBuf dp_dev;
   int tpr = 8;     // SpMV threads per row
+  bool norms_ready = false;
 
   // series workspace
   DevBuf kbuf, ring, jobs, ctrl, scratch;
@@ -98,6 +99,10 @@ template <class R> struct MfOp;
 template <class R> MfOp<R> make_mf(const Op& op, bool adjoint);
 void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
 int choose_tpr(double avg_row);
+// batch.cu
+void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
+               const double* t0s, const double* dts, const int* steps, double* const* d_pops,
+               qsw_batch_stats* stats);
 
 inline unsigned grid_for(int64_t items, int block, int max_blocks = 1 << 20) {
   int64_t b = (items + block - 1) / block;

@@ -43,21 +43,38 @@ struct Error {
   } while (0)
 
 // ------------------------------------------------------------ device memory
-// RAII device buffer (cudaMalloc/cudaFree on the context's device).
+// Stream on which the calling thread's library work runs (set at every API
+// entry from the context).  Device buffers are allocated and freed in stream
+// order on it (cudaMallocAsync / cudaFreeAsync), so freeing never synchronises
+// the whole device and concurrent streams keep running.
+inline cudaStream_t& current_stream() {
+  static thread_local cudaStream_t s = nullptr;
+  return s;
+}
+
+// RAII device buffer, stream-ordered on the stream current at allocation.
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  cudaStream_t s = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
-  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+  DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes), s(o.s) { o.p = nullptr; o.bytes = 0; }
   DevBuf& operator=(DevBuf&& o) noexcept {
-    if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+    if (this != &o) {
+      release();
+      p = o.p;
+      bytes = o.bytes;
+      s = o.s;
+      o.p = nullptr;
+      o.bytes = 0;
+    }
     return *this;
   }
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) cudaFreeAsync(p, s);
     p = nullptr;
     bytes = 0;
   }
@@ -65,7 +82,8 @@ struct DevBuf {
     if (nbytes <= bytes && p) return;
     release();
     if (nbytes == 0) return;
-    QSW_CUDA_TRY(cudaMalloc(&p, nbytes));
+    s = current_stream();
+    QSW_CUDA_TRY(cudaMallocAsync(&p, nbytes, s));
     bytes = nbytes;
   }
   template <class T> T* as() const { return static_cast<T*>(p); }

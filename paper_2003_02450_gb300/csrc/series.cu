@@ -206,7 +206,6 @@ series_kernel(SeriesArgs a) {
   __shared__ double s_step[kDMax];
   __shared__ int s_active[kDMax];
   __shared__ int s_any;
-  __shared__ int s_item;
   __shared__ double s_normk;
 
   const int tid = threadIdx.x;
@@ -625,8 +624,11 @@ int choose_tpr(double avg_row) {
   return 32;
 }
 
+void upload_theta_batch();
+
 void upload_theta(int device) {
   (void)device;
+  upload_theta_batch();
   QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta, theta_table(QSW_C128), sizeof(double) * kMMax, 0));
   QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta, theta_table(QSW_C64_BULK), sizeof(double) * kMMax,
                                   sizeof(double) * kMMax));

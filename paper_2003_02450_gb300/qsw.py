@@ -60,6 +60,31 @@ class qsw_series_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class qsw_batch_stats(ctypes.Structure):
+    _fields_ = [("walks", c_int32), ("clusters", c_int32), ("norms_ms", c_double),
+                ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+QSW_BUILD_DEFER_NORMS = 0x100
+
+
+class qsw_server_config(ctypes.Structure):
+    _fields_ = [("workers", c_int32), ("max_batch", c_int32), ("memory_budget_bytes", c_double)]
+
+
+class qsw_request(ctypes.Structure):
+    _fields_ = [("graph", qsw_csr), ("omega", c_double), ("precision", c_int32),
+                ("rho0", c_void_p), ("populations", c_void_p), ("t0", c_double),
+                ("dt", c_double), ("steps", c_int32), ("pops_out", c_void_p)]
+
+
+class qsw_request_result(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("latency_ms", c_double), ("queue_ms", c_double),
+                ("error", ctypes.c_char * 256)]
+
 _lib = None
 
 _SIGNATURES = {
@@ -83,6 +108,14 @@ _SIGNATURES = {
     "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
     "qsw_kernel_launches": ([], c_int64),
+    "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
+    "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
+    "qsw_server_wait": ([c_void_p, c_int64, c_double, POINTER(qsw_request_result)], c_int32),
+    "qsw_server_stats": ([c_void_p, POINTER(c_int64), POINTER(c_int64), POINTER(c_double)], c_int32),
+    "qsw_server_destroy": ([c_void_p], None),
+    "qsw_batch_series": ([c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p), c_int32,
+                          POINTER(c_double), POINTER(c_double), POINTER(c_int32),
+                          POINTER(c_void_p), POINTER(qsw_batch_stats)], c_int32),
     "qsw_select_params": ([POINTER(c_double), c_double, c_int32, c_int32, POINTER(c_int32),
                            POINTER(c_int32)], c_int32),
 }
@@ -176,13 +209,13 @@ def qsw_last_error(ctx) -> str:
 
 
 def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(),
-                            precision="c128", operator="matfree"):
+                            precision="c128", operator="matfree", defer_norms: bool = False):
     g = _as_csr(G)
     h = _as_csr(H)
     src, nsrc = _ports(sources)
     snk, nsnk = _ports(sinks)
     prec = PRECISIONS.get(precision, precision)
-    kind = OPERATORS.get(operator, operator)
+    kind = OPERATORS.get(operator, operator) | (QSW_BUILD_DEFER_NORMS if defer_norms else 0)
     op = c_void_p()
     st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
                                        src, nsrc, snk, nsnk, int(prec), int(kind), byref(op))
@@ -237,6 +270,68 @@ def qsw_expmv_series_host(ctx, op, h_rho0, t0: float, dt: float, steps: int, h_o
 
 def qsw_populations(ctx, op, d_rho_series, count: int, d_pops) -> None:
     _check(lib().qsw_populations(op, _ptr(d_rho_series), int(count), _ptr(d_pops)), ctx)
+
+
+def qsw_batch_series(ctx, ops, d_rho0s, n0: int, t0s, dts, steps, d_pops) -> dict:
+    """Many walks in one launch; lists of per-walk operators / device buffers."""
+    k = len(ops)
+    arr = lambda T, xs: (T * k)(*xs)
+    stats = qsw_batch_stats()
+    _check(lib().qsw_batch_series(ctx, k, arr(c_void_p, [o.value if isinstance(o, c_void_p) else o for o in ops]),
+                                  arr(c_void_p, [_ptr(x).value for x in d_rho0s]), int(n0),
+                                  arr(c_double, [float(x) for x in t0s]),
+                                  arr(c_double, [float(x) for x in dts]),
+                                  arr(c_int32, [int(x) for x in steps]),
+                                  arr(c_void_p, [_ptr(x).value for x in d_pops]), byref(stats)), ctx)
+    return stats.as_dict()
+
+
+def qsw_server_create(device: int = 0, workers: int = 2, max_batch: int = 64,
+                      memory_budget_bytes: float = 0.0):
+    h = c_void_p()
+    cfg = qsw_server_config(int(workers), int(max_batch), float(memory_budget_bytes))
+    _check(lib().qsw_server_create(int(device), byref(cfg), byref(h)))
+    return h
+
+
+class Request:
+    """Host-side request; keeps every buffer the server reads or writes alive."""
+
+    def __init__(self, G, omega, t0, dt, steps, precision="c128", rho0=None, populations=None):
+        self.g = _as_csr(G)
+        self.n = self.g.c.n
+        self.rho0 = None if rho0 is None else np.asfortranarray(np.asarray(rho0, np.complex128))
+        self.pops0 = None if populations is None else np.ascontiguousarray(populations, np.float64)
+        self.pops = np.zeros((steps + 1, self.n))
+        self.c = qsw_request(self.g.c, float(omega), int(PRECISIONS.get(precision, precision)),
+                             _ptr(self.rho0), _ptr(self.pops0), float(t0), float(dt), int(steps),
+                             _ptr(self.pops))
+        self.id = None
+
+
+def qsw_server_submit(server, req: "Request") -> int:
+    i = c_int64()
+    _check(lib().qsw_server_submit(server, byref(req.c), byref(i)))
+    req.id = i.value
+    return i.value
+
+
+def qsw_server_wait(server, req: "Request", timeout_s: float = 600.0) -> dict:
+    res = qsw_request_result()
+    st = lib().qsw_server_wait(server, int(req.id), float(timeout_s), byref(res))
+    if st != 0:
+        raise QswError(st, res.error.decode(errors="replace"))
+    return {"latency_ms": res.latency_ms, "queue_ms": res.queue_ms}
+
+
+def qsw_server_stats(server) -> dict:
+    q, b, m = c_int64(), c_int64(), c_double()
+    _check(lib().qsw_server_stats(server, byref(q), byref(b), byref(m)))
+    return {"queued": q.value, "batches": b.value, "bytes_in_use": m.value}
+
+
+def qsw_server_destroy(server) -> None:
+    lib().qsw_server_destroy(server)
 
 
 def qsw_kernel_launches() -> int:

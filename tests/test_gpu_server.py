@@ -1,0 +1,107 @@
+"""Serving loop: requests of mixed size, omega, time grid and precision
+submitted while others run; each result must match the oracle, and must be
+identical whether the request ran alone or in the mix."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from oracle import expmv, graph, superop
+from paper_2003_02450_gb300 import workloads as W
+from tests.libbuild import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(count, seed):
+    from paper_2003_02450_gb300 import qsw as C
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k in range(count):
+        n = int(round(np.exp(rng.uniform(np.log(6), np.log(48)))))
+        g = W.erdos_renyi_mean_degree(n, 3.0, seed * 1000 + k)
+        omega = float(rng.uniform(0, 1))
+        steps = int(rng.integers(1, 40))
+        prec = "c64" if k % 2 else "c128"
+        t0 = float(rng.choice([0.0, 0.3]))
+        if k % 3 == 0:
+            r = C.Request(g, omega, t0, 0.1, steps, prec, populations=np.eye(n)[0])
+            rho0 = W.basis_state(n, 0)
+        else:
+            rho0 = W.random_pure_states(n, 1, seed * 1000 + k)[0]
+            r = C.Request(g, omega, t0, 0.1, steps, prec, rho0=rho0)
+        r.meta = (g, omega, rho0, t0, steps, prec)
+        reqs.append(r)
+    return reqs
+
+
+def _oracle_pops(g, omega, rho0, t0, steps):
+    walk = graph.lqsw_walk(graph.adjacency(g))
+    L = superop.superoperator(walk, omega)
+    X = expmv.expmv_series(L, W.vec(rho0), t0, 0.1, steps)
+    return superop.populations(X, walk.n_tilde)
+
+
+def test_server_mix_matches_oracle_and_alone():
+    ensure_built()
+    from paper_2003_02450_gb300 import qsw as C
+    reqs = _requests(24, 3)
+    srv = C.qsw_server_create(0, workers=3, max_batch=8, memory_budget_bytes=64e6)
+    try:
+        # submit from two threads, staggered, so that batches overlap
+        def submit(part):
+            for r in part:
+                C.qsw_server_submit(srv, r)
+                time.sleep(0.002)
+        ths = [threading.Thread(target=submit, args=(reqs[i::2],)) for i in range(2)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        res = [C.qsw_server_wait(srv, r, 300.0) for r in reqs]
+        st = C.qsw_server_stats(srv)
+    finally:
+        C.qsw_server_destroy(srv)
+    assert st["batches"] >= 2 and st["queued"] == 0
+    for r, info in zip(reqs, res):
+        g, omega, rho0, t0, steps, prec = r.meta
+        ref = _oracle_pops(g, omega, rho0, t0, steps)
+        tol = 1e-10 if prec == "c128" else 1e-4
+        assert np.max(np.abs(r.pops - ref)) <= tol
+        assert info["latency_ms"] >= info["queue_ms"] >= 0.0
+    # alone: the same request through a fresh server, one at a time
+    srv = C.qsw_server_create(0, workers=1, max_batch=1)
+    try:
+        for r in reqs[:6]:
+            g, omega, rho0, t0, steps, prec = r.meta
+            alone = C.Request(g, omega, t0, 0.1, steps, prec, rho0=rho0)
+            C.qsw_server_submit(srv, alone)
+            C.qsw_server_wait(srv, alone, 300.0)
+            assert np.array_equal(alone.pops, r.pops)      # bit-identical alone and in the mix
+    finally:
+        C.qsw_server_destroy(srv)
+
+
+def test_server_isolates_bad_requests_and_oversized_ones():
+    ensure_built()
+    from paper_2003_02450_gb300 import qsw as C
+    good = _requests(3, 9)
+    loop = W.Digraph(3, np.array([0, 1, 1, 1], np.int32), np.array([0], np.int32), np.array([1.0]))
+    bad = C.Request(loop, 0.5, 0.0, 0.1, 3, "c128", populations=[1.0, 0, 0])
+    big = _requests(1, 11)[0]
+    srv = C.qsw_server_create(0, workers=2, max_batch=4, memory_budget_bytes=1.0)  # everything oversized
+    try:
+        for r in good + [bad, big]:
+            C.qsw_server_submit(srv, r)
+        for r in good + [big]:
+            C.qsw_server_wait(srv, r, 300.0)
+        with pytest.raises(C.QswError) as e:
+            C.qsw_server_wait(srv, bad, 300.0)
+        assert e.value.name == "QSW_ERR_NOT_SIMPLE"
+    finally:
+        C.qsw_server_destroy(srv)
+    for r in good + [big]:
+        g, omega, rho0, t0, steps, prec = r.meta
+        tol = 1e-10 if prec == "c128" else 1e-4
+        assert np.max(np.abs(r.pops - _oracle_pops(g, omega, rho0, t0, steps))) <= tol
