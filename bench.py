@@ -48,7 +48,8 @@ def parse_args():
                     help="how the series applies the superoperator")
     ap.add_argument("--no-csr-line", action="store_true",
                     help="skip the extra CSR-operator series measurement")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256"],
+    ap.add_argument("--requests", type=int, default=2000, help="serve2000: number of requests")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -446,6 +447,69 @@ def run_batch_workload(args):
     print(json.dumps(line))
 
 
+def run_serve_workload(args):
+    """Request stream: ER digraphs with mean out-degree 8, N log-uniform in
+    [32, 1024], omega ~ U(0,1), 1..100 output times of dt = 0.1, complex64 /
+    complex128 50/50, rho0 = |0><0|.  First the capacity (all requests submitted
+    at once), then Poisson arrivals at 0.5x and 0.9x that capacity; latency =
+    submit -> populations on the host."""
+    import threading
+    import numpy as np
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    specs = W.serve_requests(count=args.requests)
+    graphs = {}
+
+    def make(spec):
+        g = graphs.get(spec["graph_seed"])
+        if g is None:
+            g = W.erdos_renyi_mean_degree(spec["n"], 8.0, spec["graph_seed"])
+            graphs[spec["graph_seed"]] = g
+        return C.Request(g, spec["omega"], 0.0, spec["dt"], spec["steps"], spec["precision"],
+                         populations=np.eye(1, spec["n"])[0])
+
+    def run(rate):
+        srv = C.qsw_server_create(0, workers=4, max_batch=64)
+        reqs = [make(sp) for sp in specs]
+        rng = np.random.default_rng(123)
+        gaps = rng.exponential(1.0 / rate, size=len(reqs)) if rate else np.zeros(len(reqs))
+        t_start = time.perf_counter()
+
+        def producer():
+            t = time.perf_counter()
+            for r, gap in zip(reqs, gaps):
+                t += gap
+                delay = t - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                C.qsw_server_submit(srv, r)
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        lat = [C.qsw_server_wait(srv, r, 3600.0)["latency_ms"] for r in reqs]
+        wall = time.perf_counter() - t_start
+        st = C.qsw_server_stats(srv)
+        C.qsw_server_destroy(srv)
+        return {"requests": len(reqs), "wall_s": wall, "throughput_rps": len(reqs) / wall,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "batches": st["batches"]}
+
+    run(None) if args.warmup else None          # warm-up: page in, fill the memory pool
+    cap = run(None)
+    loads = {}
+    for load in (0.5, 0.9):
+        loads[str(load)] = run(load * cap["throughput_rps"])
+    line = {"metric": "served walk requests/s and p50/p99 latency (Poisson arrivals)",
+            "value": cap["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
+            "steps": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed c64 bulk / c128 (50/50)",
+            "data": "synthetic (seeded Erdos-Renyi digraphs, mean out-degree 8)",
+            "config": {"workload": "serve2000", "requests": len(specs), "N": "log-uniform [32, 1024]",
+                       "steps": "U{1..100}", "dt": 0.1, "workers": 4, "max_batch": 64},
+            "capacity": cap, "offered_load": loads}
+    print(json.dumps(line))
+
+
 def run_profile_case(q: int):
     import torch
     from paper_2003_02450_gb300 import qsw as C
@@ -476,6 +540,9 @@ def main():
         return
     if args.workload == "batch256":
         run_batch_workload(args)
+        return
+    if args.workload == "serve2000":
+        run_serve_workload(args)
         return
     run_ours(args)
 

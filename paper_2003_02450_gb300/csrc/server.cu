@@ -35,6 +35,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Requests with at least this many vertices (n = N^2 >= 25,600 elements) run
+// on the whole GPU; a cluster of 8 CTAs is ~3 % of the machine.
+constexpr int kWholeGpuVertices = 160;
+
 struct Req {
   int64_t id = 0;
   // inputs (host copies)
@@ -109,13 +113,23 @@ void qsw_server::worker(int wi) {
       if (queue.empty() && stopping) return;
       if (queue.empty()) continue;
       // first come, first served, as long as the memory budget allows; the
-      // head of the queue is always taken when nothing else runs
-      while (!queue.empty() && (int)take.size() < max_batch) {
-        auto& r = queue.front();
-        if (in_use + r->footprint > budget && !(in_use == 0 && take.empty())) break;
+      // head of the queue is always taken when nothing else runs.  A large
+      // walk (whole-GPU kernel) is taken alone; small walks are grouped into
+      // one batched launch and never wait behind a large one.
+      if (queue.front()->N >= kWholeGpuVertices) {
+        auto r = queue.front();
         in_use += r->footprint;
         take.push_back(r);
         queue.pop_front();
+      } else {
+        for (auto it = queue.begin(); it != queue.end() && (int)take.size() < max_batch;) {
+          auto& r = *it;
+          if (r->N >= kWholeGpuVertices) { ++it; continue; }
+          if (in_use + r->footprint > budget && !(in_use == 0 && take.empty())) break;
+          in_use += r->footprint;
+          take.push_back(r);
+          it = queue.erase(it);
+        }
       }
       if (!take.empty()) ++batches;
     }
@@ -171,9 +185,36 @@ void qsw_server::worker(int wi) {
     qsw_status st = QSW_OK;
     std::string err;
     if (!ops.empty()) {
-      qsw_batch_stats bs{};
-      st = qsw_batch_series(ctx, (int32_t)ops.size(), ops.data(), d_rho.data(), 1, t0s.data(),
-                            dts.data(), steps.data(), d_pops.data(), &bs);
+      // large walks use the whole GPU (the persistent single-walk kernel); the
+      // rest share one batched launch, a thread-block cluster each
+      std::vector<qsw_op*> bops;
+      std::vector<const double*> brho;
+      std::vector<double*> bpops;
+      std::vector<double> bt0, bdt;
+      std::vector<int> bsteps;
+      for (size_t k = 0; k < live.size(); ++k) {
+        Req& r = *live[k];
+        if (r.N >= kWholeGpuVertices) {
+          const qsw_status s1 = qsw_expmv_series(ops[k], d_rho[k], r.t0, r.dt, r.steps, nullptr,
+                                                 d_pops[k], nullptr);
+          if (s1 != QSW_OK) {
+            r.status = s1;
+            r.error = ctx->last_error;
+          }
+          continue;
+        }
+        bops.push_back(ops[k]);
+        brho.push_back(d_rho[k]);
+        bpops.push_back(d_pops[k]);
+        bt0.push_back(t0s[k]);
+        bdt.push_back(dts[k]);
+        bsteps.push_back(steps[k]);
+      }
+      if (!bops.empty()) {
+        qsw_batch_stats bs{};
+        st = qsw_batch_series(ctx, (int32_t)bops.size(), bops.data(), brho.data(), 1, bt0.data(),
+                              bdt.data(), bsteps.data(), bpops.data(), &bs);
+      }
       if (st != QSW_OK) err = ctx->last_error;
       for (size_t k = 0; k < live.size() && st == QSW_OK; ++k) {
         Req& r = *live[k];
