@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--no-csr-line", action="store_true",
                     help="skip the extra CSR-operator series measurement")
     ap.add_argument("--requests", type=int, default=2000, help="serve2000: number of requests")
+    ap.add_argument("--walks", type=int, default=256, help="batch256: number of walks")
     ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
@@ -384,7 +385,7 @@ def run_batch_workload(args):
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = C.qsw_create(0, stream.cuda_stream)
-    walks = W.batch_regular()
+    walks = W.batch_regular(count=args.walks)
     q, dt, n0 = 10, 0.2, 4
     rhos = [torch.from_numpy(np.concatenate([W.vec(s) for s in st])).to(dev) for _, _, st in walks]
     pops = [torch.empty((q + 1) * n0 * g.n, dtype=torch.float64, device=dev) for g, _, _ in walks]

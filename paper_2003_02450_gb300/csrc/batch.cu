@@ -436,36 +436,80 @@ template <> struct BC<float2> {
   __device__ static const MfOp<float>& mf(const BWalk& w) { return w.mf32; }
 };
 
-template <class VT>
-__device__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double tol, double* s_coef,
+// Truncating double -> float with integer operations only (no FP64 pipe
+// instruction); exact to 2^-23 relative, tiny values flush to zero.  Used for
+// the norms of the complex64-bulk stop test, whose tolerance is 2^-24.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const long long b = __double_as_longlong(v);
+  const int hi = (int)(b >> 32);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  const int m = (int)((b >> 29) & 0x7fffff);
+  const int bits = (hi & (int)0x80000000) | (e << 23) | m;
+  return e <= 0 ? 0.0f : __int_as_float(e >= 255 ? ((hi & (int)0x80000000) | 0x7f800000) : bits);
+}
+
+// |z| contribution of one entry to a row sum (n0 > 1) or |z|^2 (n0 = 1), in
+// the precision the stop test needs: FP32 for complex64 bulk, FP64 otherwise.
+template <bool F32, int N0> struct NormAcc;
+template <int N0> struct NormAcc<true, N0> {
+  using T = float;
+  __device__ static float of(double x, double y) {
+    const float a = f32_trunc(x), b = f32_trunc(y);
+    return N0 == 1 ? a * a + b * b : sqrtf(a * a + b * b);
+  }
+  __device__ static float of_f(float a, float b) { return N0 == 1 ? a * a + b * b : sqrtf(a * a + b * b); }
+  __device__ static float vmax(float a, float b) {   // non-negative: integer compare
+    return __int_as_float(max(__float_as_int(a), __float_as_int(b)));
+  }
+};
+template <int N0> struct NormAcc<false, N0> {
+  using T = double;
+  __device__ static double of(double x, double y) {
+    return N0 == 1 ? x * x + y * y : sqrt(x * x + y * y);
+  }
+  __device__ static double of_f(double a, double b) { return of(a, b); }
+  __device__ static double vmax(double a, double b) {
+    return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+  }
+};
+
+constexpr int kBKReg = 4;   // outputs whose running maxima live in registers
+
+template <class VT, int N0>
+__device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double tol, double* s_coef,
                          double* s_step, double* s_c1, int* s_active) {
   using Rt = typename BC<VT>::R;
+  constexpr bool kF32 = sizeof(Rt) == sizeof(float);
+  using NA = NormAcc<kF32, N0>;
+  using NT = typename NA::T;
   const int crank = (int)cl.block_rank();
   const long long ct = (long long)crank * kBT + threadIdx.x;
   const long long cstride = (long long)kCl * kBT;
   const int Nt = W.Nt;
   const long long n = W.n;
-  const int n0 = W.n0;
   const bool herm = W.herm != 0;
   const MfOp<Rt>& op = BC<VT>::mf(W);
-  VT* kcur = static_cast<VT*>(W.kbuf);
-  VT* knext = kcur + (long long)n0 * n;
   const int lane = threadIdx.x & 31;
   const int gw = crank * kBW + (threadIdx.x >> 5);
-  auto fslot = [&](int idx) { return W.fring + (long long)(idx % W.ring) * n0 * n; };
+  double2* const fring = W.fring;
+  const int ring = W.ring;
+  auto fslot = [&](int idx) { return fring + (long long)(idx % ring) * N0 * n; };
+  // per-block maxima of outputs k >= kBKReg (shared, as bit patterns)
+  unsigned long long* s_extra = reinterpret_cast<unsigned long long*>(s_c1 + kBDMax);
   long long matvecs = 0, fupd = 0;
 
   for (int jb = 0; jb < W.njobs; ++jb) {
     const Job J = W.jobs[jb];
     const double2* Z = J.z_slot < 0 ? W.rho0 : fslot(J.z_slot);
     VT* kc = static_cast<VT*>(W.kbuf);
-    VT* kn = kc + (long long)n0 * n;
+    VT* kn = kc + (long long)N0 * n;
     // init: Khat_0 = Z, F_k = Z, ||Z||_inf
-    double zn = 0.0;
+    NT zn = 0;
     for (long long r = ct; r < n; r += cstride) {
       const int i = (int)(r % Nt), j = (int)(r / Nt);
-      double rs = 0.0;
-      for (int c = 0; c < n0; ++c) {
+      NT rs = 0;
+#pragma unroll
+      for (int c = 0; c < N0; ++c) {
         double2 z;
         if (herm && i > j) {
           z = __ldcg(Z + c * n + j + (long long)Nt * i);
@@ -475,115 +519,142 @@ __device__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double t
         }
         kc[c * n + r] = BC<VT>::mk((Rt)z.x, (Rt)z.y);
         for (int k = 0; k < J.d; ++k) fslot(J.out_index0 + k)[c * n + r] = z;
-        rs += n0 == 1 ? z.x * z.x + z.y * z.y : hypot(z.x, z.y);
+        rs += NA::of(z.x, z.y);
       }
-      zn = fmax(zn, rs);
+      zn = NA::vmax(zn, rs);
     }
     double znorm, dmy;
-    cl_max2(cl, R, zn, 0.0, znorm, dmy);
-    if (n0 == 1) znorm = sqrt(znorm);
+    cl_max2(cl, R, (double)zn, 0.0, znorm, dmy);
+    if (N0 == 1) znorm = sqrt(znorm);
     for (int k = threadIdx.x; k < J.d; k += kBT) {
       s_c1[k] = znorm;
       s_coef[k] = 1.0;
       s_step[k] = (double)(k + 1) / J.d;
       s_active[k] = 1;
+      s_extra[k] = 0ULL;
     }
     __syncthreads();
     for (int p = 1; p <= J.m; ++p) {
       const Rt scale = (Rt)(J.hspan / p);
       for (int k = threadIdx.x; k < J.d; k += kBT) s_coef[k] *= s_step[k];
       __syncthreads();
-      double kmax = 0.0;
-      double fmx[kBDMax > 8 ? 8 : kBDMax];
-      for (int u = 0; u < 8; ++u) fmx[u] = 0.0;
-      double fmx_rest = 0.0;   // outputs k >= 8 are folded (only their max matters per k below)
+      double coef[kBKReg];
+      bool own[kBKReg];
+#pragma unroll
+      for (int u = 0; u < kBKReg; ++u) {
+        own[u] = u < J.d && s_active[u];
+        coef[u] = own[u] ? s_coef[u] : 0.0;
+      }
+      NT kmax = 0;
+      NT fmx[kBKReg];
+#pragma unroll
+      for (int u = 0; u < kBKReg; ++u) fmx[u] = 0;
       const long long nitems = mf_item_count(Nt, herm);
       for (long long it = gw; it < nitems; it += kCl * kBW) {
         int j, i0;
         mf_item(it, Nt, herm, j, i0);
         int irow[2];
+#pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int i = i0 + lane + 32 * u;
           irow[u] = (i < Nt && (!herm || i <= j)) ? i : -1;
         }
-        Rt yx[2][kMaxRhs], yy[2][kMaxRhs];
-        for (int c = 0; c < n0; ++c) {
+        Rt yx[2][N0], yy[2][N0];
+#pragma unroll
+        for (int c = 0; c < N0; ++c) {
           Rt cx[2], cy[2];
           mf_partB<Rt, VT, 2>(op, kc + c * n, j, irow, cx, cy);
+#pragma unroll
           for (int u = 0; u < 2; ++u) {
-            if (irow[u] < 0) continue;
-            mf_finish<Rt, VT, false>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c], yy[u][c]);
+            yx[u][c] = 0;
+            yy[u][c] = 0;
+            if (irow[u] >= 0)
+              mf_finish<Rt, VT, false>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c], yy[u][c]);
           }
         }
+#pragma unroll
         for (int u = 0; u < 2; ++u) {
           if (irow[u] < 0) continue;
           const int i = irow[u];
           const long long r = i + (long long)Nt * j;
-          double rs = 0.0;
-          for (int c = 0; c < n0; ++c) {
+          NT rs = 0;
+          double dx[N0], dy[N0];
+#pragma unroll
+          for (int c = 0; c < N0; ++c) {
             const Rt ax = yx[u][c] * scale, ay = yy[u][c] * scale;
             kn[c * n + r] = BC<VT>::mk(ax, ay);
             if (herm && i != j) kn[c * n + j + (long long)Nt * i] = BC<VT>::mk(ax, -ay);
-            yx[u][c] = ax;
-            yy[u][c] = ay;
-            rs += n0 == 1 ? (double)ax * ax + (double)ay * ay
-                          : (double)sqrtf((float)ax * (float)ax + (float)ay * (float)ay);
+            rs += NA::of_f((NT)ax, (NT)ay);
+            dx[c] = (double)ax;
+            dy[c] = (double)ay;
           }
-          kmax = fmax(kmax, rs);
-          for (int k = 0; k < J.d; ++k) {
-            if (!s_active[k]) continue;
-            double2* F = fslot(J.out_index0 + k);
-            double fs = 0.0;
-            for (int c = 0; c < n0; ++c) {
+          kmax = NA::vmax(kmax, rs);
+#pragma unroll
+          for (int u2 = 0; u2 < kBKReg; ++u2) {
+            if (!own[u2]) continue;
+            double2* F = fslot(J.out_index0 + u2);
+            NT fs = 0;
+#pragma unroll
+            for (int c = 0; c < N0; ++c) {
               double2 f = __ldcg(F + c * n + r);
-              f.x = fma(s_coef[k], (double)yx[u][c], f.x);
-              f.y = fma(s_coef[k], (double)yy[u][c], f.y);
+              f.x = fma(coef[u2], dx[c], f.x);
+              f.y = fma(coef[u2], dy[c], f.y);
               F[c * n + r] = f;
-              fs += n0 == 1 ? f.x * f.x + f.y * f.y
-                            : (double)sqrtf((float)f.x * (float)f.x + (float)f.y * (float)f.y);
+              fs += NA::of(f.x, f.y);
             }
-            if (k < 8) fmx[k] = fmax(fmx[k], fs);
-            else atomicMax(reinterpret_cast<unsigned long long*>(&s_c1[kBDMax + k]), bits_of(fs));
+            fmx[u2] = NA::vmax(fmx[u2], fs);
+          }
+          for (int k = kBKReg; k < J.d; ++k) {
+            if (!s_active[k]) continue;
+            const double ck = s_coef[k];
+            double2* F = fslot(J.out_index0 + k);
+            NT fs = 0;
+#pragma unroll
+            for (int c = 0; c < N0; ++c) {
+              double2 f = __ldcg(F + c * n + r);
+              f.x = fma(ck, dx[c], f.x);
+              f.y = fma(ck, dy[c], f.y);
+              F[c * n + r] = f;
+              fs += NA::of(f.x, f.y);
+            }
+            atomicMax(&s_extra[k], bits_of((double)fs));
           }
         }
       }
-      (void)fmx_rest;
-      // norms: K and the first outputs through cl_max2 pairs
-      double gk, g0;
-      cl_max2(cl, R, kmax, fmx[0], gk, g0);
+      // cluster maxima: K and the register outputs in pairs, the rest from s_extra
       double fn[kBDMax];
-      fn[0] = g0;
-      for (int k = 1; k < J.d && k < 8; k += 2) {
+      double gk;
+      cl_max2(cl, R, (double)kmax, (double)fmx[0], gk, fn[0]);
+#pragma unroll
+      for (int u = 1; u < kBKReg; u += 2) {
+        if (u >= J.d) break;
         double a0, a1;
-        cl_max2(cl, R, fmx[k], k + 1 < 8 ? fmx[k + 1] : 0.0, a0, a1);
-        fn[k] = a0;
-        if (k + 1 < J.d && k + 1 < 8) fn[k + 1] = a1;
+        cl_max2(cl, R, (double)fmx[u], u + 1 < kBKReg ? (double)fmx[u + 1] : 0.0, a0, a1);
+        fn[u] = a0;
+        if (u + 1 < kBKReg) fn[u + 1] = a1;
       }
-      for (int k = 8; k < J.d; ++k) {
+      for (int k = kBKReg; k < J.d; k += 2) {
         double a0, a1;
-        cl_max2(cl, R, of_bits(*reinterpret_cast<unsigned long long*>(&s_c1[kBDMax + k])), 0.0,
-                a0, a1);
+        cl_max2(cl, R, of_bits(s_extra[k]), k + 1 < J.d ? of_bits(s_extra[k + 1]) : 0.0, a0, a1);
         fn[k] = a0;
-        __syncthreads();
-        if (threadIdx.x == 0) s_c1[kBDMax + k] = 0.0;
+        if (k + 1 < J.d) fn[k + 1] = a1;
       }
       ++matvecs;
       for (int k = 0; k < J.d; ++k) fupd += s_active[k];
-      const double normk = n0 == 1 ? sqrt(gk) : gk;
+      const double normk = N0 == 1 ? sqrt(gk) : gk;
+      // stop test, identical in every CTA of the cluster
       int any = 0;
-      for (int k = 0; k < J.d; ++k) {
+      __syncthreads();
+      for (int k = threadIdx.x; k < J.d; k += kBT) {
+        s_extra[k] = 0ULL;
         if (!s_active[k]) continue;
         const double c2 = s_coef[k] * normk;
-        const double nf = n0 == 1 ? sqrt(fn[k]) : fn[k];
-        const bool stop = s_c1[k] + c2 <= tol * nf;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          if (stop) s_active[k] = 0;
-          s_c1[k] = c2;
-        }
-        __syncthreads();
-        any |= !stop;
+        const double nf = N0 == 1 ? sqrt(fn[k]) : fn[k];
+        if (s_c1[k] + c2 <= tol * nf) s_active[k] = 0;
+        s_c1[k] = c2;
       }
+      __syncthreads();
+      for (int k = 0; k < J.d; ++k) any |= s_active[k];
       VT* t = kc;
       kc = kn;
       kn = t;
@@ -591,13 +662,13 @@ __device__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double t
     }
     // populations of the finished outputs
     if (J.final_outputs && W.pops) {
-      const long long tot = (long long)J.d * n0 * Nt;
+      const long long tot = (long long)J.d * N0 * Nt;
       for (long long q = ct; q < tot; q += cstride) {
-        const int k = (int)(q / ((long long)n0 * Nt));
-        const int rem = (int)(q % ((long long)n0 * Nt));
+        const int k = (int)(q / ((long long)N0 * Nt));
+        const int rem = (int)(q % ((long long)N0 * Nt));
         const int c = rem / Nt, v = rem % Nt;
         const double2 z = __ldcg(fslot(J.out_index0 + k) + c * n + (long long)v * (Nt + 1));
-        W.pops[((long long)(J.out_index0 + k) * n0 + c) * Nt + v] = z.x;
+        W.pops[((long long)(J.out_index0 + k) * N0 + c) * Nt + v] = z.x;
       }
     }
     cl.sync();   // outputs complete before the next block reads them
@@ -606,8 +677,6 @@ __device__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double t
     W.counters[0] = matvecs;
     W.counters[1] = fupd;
   }
-  (void)kcur;
-  (void)knext;
 }
 
 __global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
@@ -633,8 +702,17 @@ batch_series_kernel(BArgs a) {
     }
     cl.sync();
     if (__ldcg(&W.counters[2])) continue;   // L2 read: every CTA sees rank 0's flag
-    if (W.f32) run_walk<float2>(cl, R, W, a.tol[1], s_coef, s_step, s_c1, s_active);
-    else run_walk<double2>(cl, R, W, a.tol[0], s_coef, s_step, s_c1, s_active);
+    const double tol = a.tol[W.f32 ? 1 : 0];
+    switch (W.n0 * 2 + W.f32) {
+      case 2: run_walk<double2, 1>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 3: run_walk<float2, 1>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 4: run_walk<double2, 2>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 5: run_walk<float2, 2>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 6: run_walk<double2, 3>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 7: run_walk<float2, 3>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      case 8: run_walk<double2, 4>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+      default: run_walk<float2, 4>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+    }
   }
 }
 
