@@ -50,7 +50,7 @@ def parse_args():
                     help="skip the extra CSR-operator series measurement")
     ap.add_argument("--requests", type=int, default=2000, help="serve2000: number of requests")
     ap.add_argument("--walks", type=int, default=256, help="batch256: number of walks")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -511,6 +511,48 @@ def run_serve_workload(args):
     print(json.dumps(line))
 
 
+def run_grid_workload(args):
+    """45 x 45 lattice (N = 2025, n = 4.1e6), omega = 0.1, rho0 = |centre><centre|,
+    20 steps of dt = 0.5: complex64 bulk (FP64 sums) and complex128, whole path
+    per step (build + series + populations)."""
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(0, stream.cuda_stream)
+    out = {}
+    for prec in ("c64", "c128"):
+        cfg = W.grid45(prec)
+        rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
+        pops = torch.empty((cfg.steps + 1, 2025), dtype=torch.float64, device=dev)
+
+        def step():
+            op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec)
+            st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, cfg.steps, None, pops)
+            C.qsw_op_destroy(op)
+            return st
+        for _ in range(max(1, args.warmup)):
+            step()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        stats = [step() for _ in range(args.steps)]
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / args.steps
+        s0 = stats[-1]
+        out[prec] = {"time_steps_per_s": cfg.steps * 1000.0 / ms, "ms_per_step": ms,
+                     "series_kernel_ms": s0["kernel_ms"], "matvecs": s0["matvecs"],
+                     "m_star": s0["m_star"], "s": s0["s"],
+                     "achieved_gbs": s0["algorithmic_bytes"] / (s0["kernel_ms"] * 1e-3) / 1e9,
+                     "achieved_tflops": s0["algorithmic_flops"] / (s0["kernel_ms"] * 1e-3) / 1e12}
+    C.qsw_destroy(ctx)
+    print(json.dumps({"metric": "walk time-steps/s (45x45 lattice, 20 steps of 0.5)",
+                      "value": out["c64"]["time_steps_per_s"], "unit": "time-steps/s",
+                      "config": {"workload": "grid45"}, "c64": out["c64"], "c128": out["c128"]}))
+
+
 def run_profile_case(q: int):
     import torch
     from paper_2003_02450_gb300 import qsw as C
@@ -544,6 +586,9 @@ def main():
         return
     if args.workload == "serve2000":
         run_serve_workload(args)
+        return
+    if args.workload == "grid45":
+        run_grid_workload(args)
         return
     run_ours(args)
 

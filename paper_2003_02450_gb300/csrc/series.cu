@@ -154,6 +154,35 @@ __device__ bool grid_barrier(Ctrl* c) {
   return s_ok != 0;
 }
 
+// Keys of the running inf-norm maxima: squared moduli as integer bit patterns
+// (non-negative numbers order like their bits), so the max never touches the
+// FP64 pipe.  complex128 keeps FP64 moduli; complex64 bulk takes them in FP32
+// (the F accumulators through an integer-only truncation to float), which is
+// ample for its 2^-24 stop test.
+__device__ __forceinline__ float f32_trunc(double v) {
+  const long long b = __double_as_longlong(v);
+  const int hi = (int)(b >> 32);
+  const int e = ((hi >> 20) & 0x7ff) - 1023 + 127;
+  const int m = (int)((b >> 29) & 0x7fffff);
+  const int bits = (hi & (int)0x80000000) | (e << 23) | m;
+  return e <= 0 ? 0.0f : __int_as_float(e >= 255 ? ((hi & (int)0x80000000) | 0x7f800000) : bits);
+}
+
+template <class VT> struct NormKey;
+template <> struct NormKey<double2> {
+  __device__ static unsigned long long y(double a, double b) { return as_bits(a * a + b * b); }
+  __device__ static unsigned long long f(double a, double b) { return as_bits(a * a + b * b); }
+  __device__ static double value(unsigned long long k) { return from_bits(k); }
+};
+template <> struct NormKey<float2> {
+  __device__ static unsigned long long y(float a, float b) { return __float_as_uint(a * a + b * b); }
+  __device__ static unsigned long long f(double a, double b) {
+    const float x = f32_trunc(a), z = f32_trunc(b);
+    return __float_as_uint(x * x + z * z);
+  }
+  __device__ static double value(unsigned long long k) { return (double)__uint_as_float((unsigned)k); }
+};
+
 // Per-thread epilogue state of one Taylor term.
 template <class VT> struct Epilogue {
   using R = typename Cplx<VT>::R;
@@ -166,12 +195,12 @@ template <class VT> struct Epilogue {
   unsigned long long fmax[kKReg];
   const double* s_coef;
   const int* s_active;
-  unsigned long long* s_fmax_extra;   // outputs k >= kKReg (shared, block-level)
+  unsigned long long* s_fmax_extra;   // outputs k >= kKReg (shared, block-level keys)
 
   __device__ void consume(long long r, R yx, R yy) {
     knext[r] = Cplx<VT>::make(yx, yy);
+    kmax = umax64(kmax, NormKey<VT>::y(yx, yy));
     const double dx = (double)yx, dy = (double)yy;
-    kmax = umax64(kmax, as_bits(dx * dx + dy * dy));
 #pragma unroll
     for (int u = 0; u < kKReg; ++u) {
       if (own[u]) {
@@ -180,7 +209,7 @@ template <class VT> struct Epilogue {
         f.x = fma(coef[u], dx, f.x);
         f.y = fma(coef[u], dy, f.y);
         *F = f;
-        fmax[u] = umax64(fmax[u], as_bits(f.x * f.x + f.y * f.y));
+        fmax[u] = umax64(fmax[u], NormKey<VT>::f(f.x, f.y));
       }
     }
     for (int k = kKReg; k < d; ++k) {
@@ -190,7 +219,7 @@ template <class VT> struct Epilogue {
       f.x = fma(s_coef[k], dx, f.x);
       f.y = fma(s_coef[k], dy, f.y);
       *F = f;
-      atomicMax(&s_fmax_extra[k], as_bits(f.x * f.x + f.y * f.y));
+      atomicMax(&s_fmax_extra[k], NormKey<VT>::f(f.x, f.y));
     }
   }
 };
@@ -389,7 +418,7 @@ series_kernel(SeriesArgs a) {
         } else {
           m = s_fmax_extra[q - 1];
         }
-        atomicMax(&ctrl->gmax[slot3][q], m);
+        atomicMax(&ctrl->gmax[slot3][q], as_bits(NormKey<VT>::value(m)));
       }
       if (blockIdx.x == 0) {
         const unsigned nx = (term + 1) % 3;
