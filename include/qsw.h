@@ -212,6 +212,42 @@ qsw_status qsw_expmv_series(qsw_op* op, const double* d_rho0, double t0, double 
                             int32_t steps, double* d_out, double* d_pops,
                             qsw_series_stats* stats);
 
+/* Size of the fixed device scratch behind qsw_expmv_series_noalloc. */
+#define QSW_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* qsw_expmv_series without any device allocation.  The paper has no
+ * counterpart: this is a property of the library, not of the method.
+ *
+ * Same arguments, results, errors and synchronisation as qsw_expmv_series,
+ * but the call's workspace (control words, the Taylor block plan, the two
+ * Taylor-term vectors and, when d_out is NULL, the ring of output slots)
+ * lives in one array of QSW_NOALLOC_SCRATCH_BYTES per device, reserved when
+ * the library's module loads.  Nothing in the call asks cudaMalloc,
+ * cudaMallocAsync or any other allocator for memory.  It is for callers that
+ * cannot allocate: a serving process whose device memory has been handed in
+ * full to another allocator's pool (an allocation would fail or evict that
+ * pool's cache), and latency-bound loops where an allocation or free may
+ * wait on other work on the device.
+ *
+ * - The operator must already hold its 1-norm series: one built without
+ *   QSW_BUILD_DEFER_NORMS, or used once by qsw_expmv_series.  Otherwise
+ *   INVALID_ARG (computing the norms needs workspace).
+ * - A series whose workspace exceeds QSW_NOALLOC_SCRATCH_BYTES is rejected
+ *   with TOO_LARGE before any work is issued.  The workspace is
+ *   (2 n + ring n) complex values plus the plan: with d_out given (no
+ *   ring) about 2 n x 16 bytes for QSW_C128, i.e. N~ up to ~700.
+ * - The call clears the parts that must start at zero itself (the control
+ *   words and the Hermiticity-check accumulators).
+ * - The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, checked; CUDA error otherwise); make that first
+ *   call before any stream capture.
+ * - Every call on a device shares the array: calls in flight at the same time
+ *   on one device (other threads, contexts or streams) race.
+ * - stats->kernel_ms is 0 (no timing events are created). */
+qsw_status qsw_expmv_series_noalloc(qsw_op* op, const double* d_rho0, double t0, double dt,
+                                    int32_t steps, double* d_out, double* d_pops,
+                                    qsw_series_stats* stats);
+
 /* Same computation with HOST buffers: h_rho0 (n complex128), h_out / h_pops
  * as d_out / d_pops above but in host memory (pinned memory is fastest).  The
  * host<->device copies are part of the call. */

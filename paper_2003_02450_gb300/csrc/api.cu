@@ -354,6 +354,20 @@ qsw_status qsw_expmv_series(qsw_op* h, const double* d_rho0, double t0, double d
   });
 }
 
+qsw_status qsw_expmv_series_noalloc(qsw_op* h, const double* d_rho0, double t0, double dt,
+                                    int32_t steps, double* d_out, double* d_pops,
+                                    qsw_series_stats* stats) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    check_series_args(op, d_rho0, t0, dt, steps, d_out, d_pops);
+    QSW_CHECK_ARG(op->norms_ready, QSW_ERR_INVALID_ARG,
+                  "operator built with QSW_BUILD_DEFER_NORMS: its norms need workspace; "
+                  "run qsw_expmv_series once first");
+    set_device(op->ctx);
+    qsw::run_series_noalloc(*op, d_rho0, t0, dt, steps, d_out, d_pops, stats);
+  });
+}
+
 qsw_status qsw_expmv_series_host(qsw_op* h, const double* h_rho0, double t0, double dt,
                                  int32_t steps, double* h_out, double* h_pops,
                                  qsw_series_stats* stats) {

@@ -29,6 +29,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "matfree.cuh"
 #include "op.h"
@@ -824,6 +826,159 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
     }
     stats->hermitian = herm ? 1 : 0;
     stats->kernel_ms = ms;
+  }
+}
+
+// ----------------------------------------------- series without allocation
+// Scratch of qsw_expmv_series_noalloc: one fixed array per device, reserved
+// when the module loads, so the call itself never asks the allocator for
+// memory.  Layout per call (each part starts on a 256-byte boundary):
+//   Ctrl | Hermiticity-check words | Job[njobs] | K0 K1 | output ring
+// Ctrl and the check words must start at zero and are cleared by every call;
+// the rest is written before it is read.  Every call on a device uses the
+// same array: two calls in flight at the same time on one device race.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[QSW_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kNoAllocDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoAllocDevices] = {};
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Device address of g_noalloc_scratch on the current device, looked up once
+// per device (the first call on a device does this set-up).
+unsigned char* noalloc_base(int device) {
+  QSW_CHECK_ARG(device >= 0 && device < kNoAllocDevices, QSW_ERR_INVALID_ARG,
+                "device index beyond the no-allocation scratch table");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_base[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      throw Error{QSW_ERR_CUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") +
+                                    cudaGetErrorString(e)};
+    g_noalloc_base[device] = p;
+  }
+  return static_cast<unsigned char*>(g_noalloc_base[device]);
+}
+
+}  // namespace
+
+void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int steps,
+                        double* d_out, double* d_pops, qsw_series_stats* stats) {
+  cudaStream_t st = op.ctx->stream;
+  const int prec = op.precision == QSW_C64_BULK ? 1 : 0;
+  const double* theta = theta_table(op.precision);
+  const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0);
+  QSW_CHECK_ARG(info.max_d <= kDMax, QSW_ERR_INVALID_ARG,
+                "more than " + std::to_string(kDMax) + " outputs per Taylor block (steps/s too large)");
+  const int ring = d_out ? 0 : info.max_d + 1;
+  const bool f32 = op.precision == QSW_C64_BULK;
+  const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
+
+  const size_t off_herm = align256(sizeof(Ctrl));
+  const size_t off_jobs = off_herm + align256(2 * sizeof(unsigned long long));
+  const size_t off_k = off_jobs + align256(sizeof(Job) * (size_t)std::max(1, info.njobs));
+  const size_t off_ring = off_k + align256(2 * vbytes * (size_t)op.n);
+  const size_t need = off_ring + sizeof(double2) * (size_t)op.n * (size_t)ring;
+  if (need > (size_t)QSW_NOALLOC_SCRATCH_BYTES)
+    throw Error{QSW_ERR_TOO_LARGE,
+                "series needs " + std::to_string(need) + " bytes of scratch; the no-allocation "
+                "entry point has " + std::to_string((size_t)QSW_NOALLOC_SCRATCH_BYTES) +
+                " (use qsw_expmv_series, or pass d_out to drop the output ring)"};
+
+  unsigned char* base = noalloc_base(op.ctx->device);
+  Ctrl* ctrl = reinterpret_cast<Ctrl*>(base);
+  unsigned long long* hwords = reinterpret_cast<unsigned long long*>(base + off_herm);
+  Job* jobs = reinterpret_cast<Job*>(base + off_jobs);
+  void* kbuf = base + off_k;
+  double2* ringbuf = reinterpret_cast<double2*>(base + off_ring);
+
+  QSW_CUDA_TRY(cudaMemsetAsync(ctrl, 0, sizeof(Ctrl), st));
+  QSW_LAUNCH plan_kernel<<<1, 32, 0, st>>>(op.dp_dev.as<double>(), prec, t0, dt, steps, 1, ring,
+                                           jobs, info.njobs, info.njobs, ctrl);
+  QSW_CUDA_TRY(cudaGetLastError());
+
+  bool herm = false;
+  if (op.opkind == QSW_OPERATOR_MATRIX_FREE) {
+    QSW_CUDA_TRY(cudaMemsetAsync(hwords, 0, 2 * sizeof(unsigned long long), st));
+    QSW_LAUNCH herm_check_kernel<<<grid_for(op.n, 256, 152 * 8), 256, 0, st>>>(
+        op.Nt, reinterpret_cast<const double2*>(d_rho0), hwords);
+    QSW_CUDA_TRY(cudaGetLastError());
+    unsigned long long hb[2] = {0, 0};
+    QSW_CUDA_TRY(cudaMemcpyAsync(hb, hwords, sizeof(hb), cudaMemcpyDeviceToHost, st));
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    double asym2, max2;
+    memcpy(&asym2, &hb[0], sizeof(double));
+    memcpy(&max2, &hb[1], sizeof(double));
+    herm = sqrt(asym2) <= 1e-13 * (sqrt(max2) > 1.0 ? sqrt(max2) : 1.0);
+  }
+
+  SeriesArgs a{};
+  a.n = (int)op.n;
+  a.nt = op.Nt;
+  a.mirror = herm && d_out != nullptr;
+  if (op.opkind == QSW_OPERATOR_CSR) {
+    a.rowptr = op.L.rowptr.as<int>();
+    a.col = op.L.col.as<int>();
+    a.val = op.L.val.p;
+  } else {
+    a.mf64 = make_mf<double>(op, false);
+    a.mf32 = make_mf<float>(op, false);
+  }
+  a.k0 = kbuf;
+  a.k1 = static_cast<char*>(kbuf) + vbytes * (size_t)op.n;
+  a.rho0 = reinterpret_cast<const double2*>(d_rho0);
+  a.slots = d_out ? reinterpret_cast<double2*>(d_out) : ringbuf;
+  a.ring = ring;
+  a.pops = d_pops;
+  a.jobs = jobs;
+  a.njobs = info.njobs;
+  a.ctrl = ctrl;
+  a.tol = tolerance(op.precision);
+
+  int grid = 0;
+  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid);
+  QSW_CUDA_TRY(e);
+  Ctrl h{};
+  QSW_CUDA_TRY(cudaMemcpyAsync(&h, ctrl, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  if (h.error == kErrBarrier)
+    throw Error{QSW_ERR_NOT_CONVERGED, "series kernel: grid barrier wait exceeded its limit"};
+  if (h.error == kErrPlan)
+    throw Error{QSW_ERR_CUDA, "series kernel: device plan differs from host plan"};
+  if (stats) {
+    // Same figures as qsw_expmv_series except kernel_ms (no timing events).
+    stats->m0 = info.m0;
+    stats->s0 = info.s0;
+    stats->m_star = info.m_star;
+    stats->s = info.s;
+    stats->step_m = info.step_m;
+    stats->step_s = info.step_s;
+    stats->outputs_per_block = info.d;
+    stats->jobs = info.njobs;
+    stats->matvecs = (int64_t)h.matvecs;
+    stats->fupdates = (int64_t)h.fupdates;
+    // outputs initialised per call: one per stage of the first state, then
+    // one per dt sub-step (steps <= s) or one per output (Algorithm 5.2)
+    const double outputs_init =
+        (double)info.s0 + (steps > 0 ? (steps <= info.s ? (double)steps * info.step_s : steps) : 0.0);
+    const double init_bytes =
+        (16.0 + vbytes) * (double)op.n * info.njobs + 16.0 * (double)op.n * outputs_init;
+    const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
+    const double elems = frac * (double)op.n;
+    const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
+    const double flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems +
+                                    4.0 * op.g.n_jumps + 5.0 * elems;
+    stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes;
+    stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
+                               32.0 * elems * (double)h.fupdates + init_bytes;
+    stats->algorithmic_flops = stats->matvecs * flops_per_matvec + 7.0 * elems * h.fupdates;
+    stats->hermitian = herm ? 1 : 0;
+    stats->kernel_ms = 0.0;
   }
 }
 

@@ -69,6 +69,7 @@ class qsw_batch_stats(ctypes.Structure):
 
 
 QSW_BUILD_DEFER_NORMS = 0x100
+NOALLOC_SCRATCH_BYTES = 16 << 20   # QSW_NOALLOC_SCRATCH_BYTES
 
 
 class qsw_server_config(ctypes.Structure):
@@ -103,6 +104,8 @@ _SIGNATURES = {
     "qsw_apply": ([c_void_p, c_void_p, c_void_p], c_int32),
     "qsw_expmv_series": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p, c_void_p,
                           POINTER(qsw_series_stats)], c_int32),
+    "qsw_expmv_series_noalloc": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p,
+                                  c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_expmv_series_host": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p,
                                c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
@@ -257,6 +260,16 @@ def qsw_expmv_series(ctx, op, d_rho0, t0: float, dt: float, steps: int, d_out=No
     stats = qsw_series_stats()
     _check(lib().qsw_expmv_series(op, _ptr(d_rho0), float(t0), float(dt), int(steps),
                                   _ptr(d_out), _ptr(d_pops), byref(stats)), ctx)
+    return stats.as_dict()
+
+
+def qsw_expmv_series_noalloc(ctx, op, d_rho0, t0: float, dt: float, steps: int, d_out=None,
+                             d_pops=None) -> dict:
+    """qsw_expmv_series with its workspace in the library's fixed device array
+    (NOALLOC_SCRATCH_BYTES per device); no device allocation in the call."""
+    stats = qsw_series_stats()
+    _check(lib().qsw_expmv_series_noalloc(op, _ptr(d_rho0), float(t0), float(dt), int(steps),
+                                          _ptr(d_out), _ptr(d_pops), byref(stats)), ctx)
     return stats.as_dict()
 
 
