@@ -263,6 +263,43 @@ __global__ void prep_mf_kernel(int N, int Nt, double omw, const int* __restrict_
   for (int e = t0; e < njt; e += nth) jtval32[e] = (float)jtval[e];
 }
 
+// Lane order of each 64-row window of the matrix-free sweep.  Part A of C
+// costs a lane the H row lengths of its two rows.  In natural order (lane l:
+// rows l and 32 + l) a warp runs max_l len(l) + max_l len(32 + l) iterations;
+// with the rows ranked by length (ties by index; rows past Nt rank first with
+// length -1) and lane l taking ranks l and 63 - l as one merged list, it runs
+// max_l (len(rank l) + len(rank 63 - l)).  The window is paired when that is
+// at most 85 % of the natural cost (the merged list costs a few selects per
+// term; uniform-degree windows keep the natural order).  One block of 64
+// threads per window.
+__global__ void window_rows_kernel(int N, int Nt, const int* __restrict__ hrow, int* prow,
+                                   int* pwin) {
+  __shared__ int len[64];
+  __shared__ int by_rank[64];
+  __shared__ int cost_nat[2], cost_pair;
+  const int k = threadIdx.x, w0 = blockIdx.x * 64;
+  const int i = w0 + k;
+  len[k] = i < Nt ? (i < N ? hrow[i + 1] - hrow[i] : 0) : -1;
+  if (k < 2) cost_nat[k] = 0;
+  if (k == 0) cost_pair = 0;
+  __syncthreads();
+  int rank = 0;
+  for (int q = 0; q < 64; ++q)
+    rank += (len[q] < len[k]) || (len[q] == len[k] && q < k);
+  by_rank[rank] = k;
+  atomicMax(&cost_nat[k >> 5], len[k] > 0 ? len[k] : 0);
+  __syncthreads();
+  if (k < 32) {
+    const int la = len[by_rank[k]], lb = len[by_rank[63 - k]];
+    atomicMax(&cost_pair, (la > 0 ? la : 0) + (lb > 0 ? lb : 0));
+  }
+  __syncthreads();
+  const bool paired = 100 * cost_pair <= 85 * (cost_nat[0] + cost_nat[1]);
+  const int slot = paired ? (rank < 32 ? rank : 32 + (63 - rank)) : k;
+  prow[w0 + slot] = i < Nt ? i : -1;
+  if (k == 0) pwin[blockIdx.x] = paired ? 1 : 0;
+}
+
 template <class T>
 void upload(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
   b.alloc(sizeof(T) * (h.size() ? h.size() : 1));
@@ -407,6 +444,13 @@ void prep_matfree(Op& op) {
       m.ad64.as<double>(), m.ad32.as<float>(), m.hw64.as<double>(), m.hw32.as<float>(),
       m.habs.as<double>(), g.j_val.as<double>(), m.jval32.as<float>(), g.n_jumps,
       g.jt_val.as<double>(), m.jtval32.as<float>(), g.n_jumps);
+  QSW_CUDA_TRY(cudaGetLastError());
+  const int nwin = (Nt + 63) / 64;
+  m.prow.alloc(sizeof(int) * 64 * (size_t)nwin);
+  m.pwin.alloc(sizeof(int) * (size_t)nwin);
+  QSW_LAUNCH window_rows_kernel<<<nwin, 64, 0, st>>>(op.omega < 1.0 ? g.N : 0, Nt,
+                                                     g.hoff_rowptr.as<int>(), m.prow.as<int>(),
+                                                     m.pwin.as<int>());
   QSW_CUDA_TRY(cudaGetLastError());
   // entries of the CSR form: diagonal + commutator stripes/blocks + one per jump
   const long long n = (long long)Nt * Nt;

@@ -32,9 +32,22 @@ template <class R> struct MfOp {
   const int* jrow;     // [Nt + 1] jumps into i (L) or out of i (L^H)
   const int* jcol;
   const R* jval;
+  const int* prow;     // [64 ceil(Nt / 64)] rows of each 64-row window in lane
+                       // order (see mf_window_rows); -1 pads the last window
+  const int* pwin;     // [ceil(Nt / 64)] 1: the window's rows are paired (part A
+                       // by mf_partA2), 0: natural order (part A row by row)
 };
 
 template <class T> __device__ __forceinline__ T ldcg_t(const T* p) { return __ldcg(p); }
+
+// Reads of the operand x.  Inside the persistent series kernel x was written
+// by other SMs before the last grid (or cluster) barrier, whose fences form a
+// gpu-scope (cluster-scope) release/acquire pair with those writes; a weak
+// load ordered after that acquire must return the new values, so x may be
+// cached in L1 (ld.global.ca).  The non-coherent read-only path (ld.global.nc)
+// would not be covered and is not used.  Part A of C reads one column of x
+// about 20 times per element, which L1 serves instead of L2.
+template <class VT> __device__ __forceinline__ VT ldx(const VT* p) { return __ldca(p); }
 
 // Part B of C for RPT rows of one column, accumulated with a minus sign:
 // c = -sum_{m in H row j} c_mj x_(i,m)  (the uniform list, coalesced over i).
@@ -45,13 +58,14 @@ __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict
   for (int u = 0; u < RPT; ++u) { cx[u] = 0; cy[u] = 0; }
   if (j >= op.N) return;
   const int e0 = op.hrow[j], e1 = op.hrow[j + 1];
+#pragma unroll 2
   for (int e = e0; e < e1; ++e) {
     const long long off = (long long)op.Nt * op.hcol[e];
     const R h = op.hval[e];
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (irow[u] >= 0) {
-        const VT v = __ldcg(x + off + irow[u]);
+        const VT v = ldx(x + off + irow[u]);
         cx[u] = fma(-h, v.x, cx[u]);
         cy[u] = fma(-h, v.y, cy[u]);
       }
@@ -59,22 +73,48 @@ __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict
   }
 }
 
-// The rest of element (i, j): part A (added to the same accumulators), the
-// diagonal and the jumps; returns (L x)_(i,j) or (L^H x)_(i,j).
-template <class R, class VT, bool ADJ>
-__device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
-                                          R cx, R cy, R& yx, R& yy) {
+// Part A of C for the two rows a = irow[0], b = irow[1] of one lane (same
+// column j): c += sum_{m in H row i} c_im x_(m,j).  The rows' entries run as one
+// list (a's, then b's) with the accumulator picked by a select, so a lane's
+// trip count is len(a) + len(b); the windows pair short rows with long ones
+// (mf_window_rows) to make that sum nearly equal across a warp.  Each row's
+// terms are added in the same order as a loop over that row alone.
+template <class R, class VT>
+__device__ __forceinline__ void mf_partA2(const MfOp<R>& op, const VT* __restrict__ x, int j,
+                                          const int* irow, R* cx, R* cy) {
   const long long base = (long long)op.Nt * j;
-  if (i < op.N) {
-    const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
-    for (int e = e0; e < e1; ++e) {
-      const VT v = __ldcg(x + base + op.hcol[e]);
-      const R h = op.hval[e];
-      cx = fma(h, v.x, cx);
-      cy = fma(h, v.y, cy);
-    }
+  const int a = irow[0], b = irow[1];
+  const int ea = (a >= 0 && a < op.N) ? op.hrow[a] : 0;
+  const int la = (a >= 0 && a < op.N) ? op.hrow[a + 1] - ea : 0;
+  const int eb = (b >= 0 && b < op.N) ? op.hrow[b] : 0;
+  const int lb = (b >= 0 && b < op.N) ? op.hrow[b + 1] - eb : 0;
+  R ax = cx[0], ay = cy[0], bx = cx[1], by = cy[1];
+  const int tot = la + lb;
+  for (int t = 0; t < tot; ++t) {
+    const bool second = t >= la;
+    const int e = second ? eb + (t - la) : ea + t;
+    const VT v = ldx(x + base + op.hcol[e]);
+    const R h = op.hval[e];
+    const R tx = fma(h, v.x, second ? bx : ax);
+    const R ty = fma(h, v.y, second ? by : ay);
+    ax = second ? ax : tx;
+    ay = second ? ay : ty;
+    bx = second ? tx : bx;
+    by = second ? ty : by;
   }
-  const VT xs = __ldcg(x + base + i);
+  cx[0] = ax;
+  cy[0] = ay;
+  cx[1] = bx;
+  cy[1] = by;
+}
+
+// Element (i, j) once C is complete: the diagonal and the jumps; returns
+// (L x)_(i,j) or (L^H x)_(i,j).
+template <class R, class VT, bool ADJ>
+__device__ __forceinline__ void mf_tail(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
+                                        R cx, R cy, R& yx, R& yy) {
+  const long long base = (long long)op.Nt * j;
+  const VT xs = ldx(x + base + i);
   const R dx = op.ad[i] + op.ad[j];
   const R dy = op.hw[j] - op.hw[i];
   R rx, ry;
@@ -88,7 +128,7 @@ __device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restric
   if (i == j) {
     const int e0 = op.jrow[i], e1 = op.jrow[i + 1];
     for (int e = e0; e < e1; ++e) {
-      const VT v = __ldcg(x + (long long)op.jcol[e] * (op.Nt + 1));
+      const VT v = ldx(x + (long long)op.jcol[e] * (op.Nt + 1));
       const R r = op.jval[e];
       rx = fma(r, v.x, rx);
       ry = fma(r, v.y, ry);
@@ -98,11 +138,63 @@ __device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restric
   yy = ry;
 }
 
+// The rest of element (i, j): part A (added to the same accumulators), the
+// diagonal and the jumps; returns (L x)_(i,j) or (L^H x)_(i,j).
+template <class R, class VT, bool ADJ>
+__device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
+                                          R cx, R cy, R& yx, R& yy) {
+  const long long base = (long long)op.Nt * j;
+  if (i < op.N) {
+    const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const VT v = ldx(x + base + op.hcol[e]);
+      const R h = op.hval[e];
+      cx = fma(h, v.x, cx);
+      cy = fma(h, v.y, cy);
+    }
+  }
+  mf_tail<R, VT, ADJ>(op, x, i, j, cx, cy, yx, yy);
+}
+
+// Rows of one 64-row window for a lane: (prow[w0 + lane], prow[w0 + 32 + lane]),
+// -1 where there is no row (past Nt, or past `last` in a Hermitian chunk).
+// Paired windows list the rows so that lane l holds ranks l and 63 - l by H
+// row length; the others list them in natural order (lane l: rows w0 + l and
+// w0 + 32 + l).
+__device__ __forceinline__ void mf_window_rows(const int* prow, int w0, int lane, int last,
+                                               int* irow) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u) {
+    const int i = prow[w0 + lane + 32 * u];
+    irow[u] = (i >= 0 && i <= last) ? i : -1;
+  }
+}
+
 // Work items of one matrix-free pass: 64-row chunks of the columns j.  In the
 // Hermitian form only rows i <= j are computed, so column j has
 // floor(j / 64) + 1 chunks and the items before column j number
 // P(j) = j + 64 a(a-1)/2 + a b  (j = 64 a + b).
 constexpr int kItemRows = 64;
+
+// C for the two rows of one lane in window w0 of column j, then the element
+// values y = (L x) or (L^H x) (scaled by the caller): part B (uniform), part A
+// (merged over the pair when the window is paired), the diagonal and jumps.
+template <class R, class VT, bool ADJ>
+__device__ __forceinline__ void mf_window_apply(const MfOp<R>& op, const VT* __restrict__ x, int j,
+                                                int w0, const int* irow, R* yx, R* yy) {
+  R cx[2], cy[2];
+  mf_partB<R, VT, 2>(op, x, j, irow, cx, cy);
+  if (op.pwin[w0 / kItemRows]) {
+    mf_partA2<R, VT>(op, x, j, irow, cx, cy);
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (irow[u] >= 0) mf_tail<R, VT, ADJ>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
+  } else {
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+      if (irow[u] >= 0) mf_finish<R, VT, ADJ>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
+  }
+}
 
 __device__ __forceinline__ long long herm_items_before(int j) {
   const long long a = j / kItemRows, b = j % kItemRows;

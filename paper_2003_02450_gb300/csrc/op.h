@@ -45,6 +45,8 @@ struct MfData {
   DevBuf hw64, hw32;       // (1 - omega) H_vv
   DevBuf jval32, jtval32;  // jump rates (FP64 copies live in GraphDev)
   DevBuf habs;             // [Nt] sum_m |(1 - omega) H_vm|, for the exact 1-norm
+  DevBuf prow;             // [64 ceil(Nt / 64)] lane order of each 64-row window
+  DevBuf pwin;             // [ceil(Nt / 64)] 1 where that order pairs the rows
 };
 
 struct Op {

@@ -338,20 +338,14 @@ series_kernel(SeriesArgs a) {
           int j, i0;
           mf_item(k, nt, kHerm, j, i0);
           int irow[kRpt];
-#pragma unroll
-          for (int u = 0; u < kRpt; ++u) {
-            const int i = i0 + lane + 32 * u;
-            irow[u] = (i < nt && (!kHerm || i <= j)) ? i : -1;
-          }
-          R cx[kRpt], cy[kRpt];
-          mf_partB<R, VT, kRpt>(op, kcur, j, irow, cx, cy);
+          mf_window_rows(op.prow, i0, lane, kHerm ? j : nt - 1, irow);
+          R ox[kRpt], oy[kRpt];
+          mf_window_apply<R, VT, false>(op, kcur, j, i0, irow, ox, oy);
 #pragma unroll
           for (int u = 0; u < kRpt; ++u) {
             if (irow[u] < 0) continue;
-            R yx, yy;
-            mf_finish<R, VT, false>(op, kcur, irow[u], j, cx[u], cy[u], yx, yy);
-            yx *= rscale;
-            yy *= rscale;
+            const R yx = ox[u] * rscale;
+            const R yy = oy[u] * rscale;
             ep.consume(irow[u] + (long long)nt * j, yx, yy);
             // Hermitian form: the term is stored in full, its lower triangle
             // as the conjugate (sign flip on the bit pattern, no FP64 op)
@@ -505,25 +499,20 @@ template <class R, class VT, bool ADJ>
 __global__ void __launch_bounds__(kBlock)
 mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__ y, double scale) {
   const long long n = (long long)op.Nt * op.Nt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = blockIdx.x; j < op.Nt; j += gridDim.x) {
-    for (int i0 = 0; i0 < op.Nt; i0 += kBlock * kRpt) {
+    for (int i0 = warp * kItemRows; i0 < op.Nt; i0 += kWarps * kItemRows) {
       int irow[kRpt];
-#pragma unroll
-      for (int u = 0; u < kRpt; ++u) {
-        const int i = i0 + threadIdx.x + u * kBlock;
-        irow[u] = i < op.Nt ? i : -1;
-      }
+      mf_window_rows(op.prow, i0, lane, op.Nt - 1, irow);
       for (int c = 0; c < cols; ++c) {
         const VT* xc = x + c * n;
-        R bx[kRpt], by[kRpt];
-        mf_partB<R, VT, kRpt>(op, xc, j, irow, bx, by);
+        R ox[kRpt], oy[kRpt];
+        mf_window_apply<R, VT, ADJ>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
         for (int u = 0; u < kRpt; ++u) {
           if (irow[u] < 0) continue;
-          R yx, yy;
-          mf_finish<R, VT, ADJ>(op, xc, irow[u], j, bx[u], by[u], yx, yy);
           y[c * n + irow[u] + (long long)op.Nt * j] =
-              Cplx<VT>::make(yx * (R)scale, yy * (R)scale);
+              Cplx<VT>::make(ox[u] * (R)scale, oy[u] * (R)scale);
         }
       }
     }
@@ -680,6 +669,8 @@ template <class R> MfOp<R> make_mf(const Op& op, bool adjoint) {
   o.jcol = adjoint ? op.g.jt_col.as<int>() : op.g.j_col.as<int>();
   o.jval = static_cast<const R*>(adjoint ? (f ? m.jtval32.p : op.g.jt_val.p)
                                          : (f ? m.jval32.p : op.g.j_val.p));
+  o.prow = m.prow.as<int>();
+  o.pwin = m.pwin.as<int>();
   return o;
 }
 template MfOp<double> make_mf<double>(const Op&, bool);
