@@ -198,6 +198,27 @@ class WalkConfig:
     note: str = ""
 
 
+def unit_ball_points(n: int, seed: int) -> np.ndarray:
+    """n points uniform in the unit ball: isotropic direction, radius U^(1/3)."""
+    rng = np.random.default_rng(seed)
+    x = rng.standard_normal((n, 3))
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    return x * rng.uniform(0.0, 1.0, size=(n, 1)) ** (1.0 / 3.0)
+
+
+def dipole_network(n: int, seed: int):
+    """Disordered network of n dipoles uniform in the unit ball (Section 4.1.4):
+    V_ij = -d_ij^-3 (i != j).  Returns (G, H): the complete digraph with arc
+    weights |V_ij| = d_ij^-3 (jump rates) and H = V as a dense symmetric matrix."""
+    x = unit_ball_points(n, seed)
+    d = np.linalg.norm(x[:, None, :] - x[None, :, :], axis=2)
+    off = ~np.eye(n, dtype=bool)
+    V = np.zeros((n, n))
+    V[off] = -d[off] ** -3.0
+    dst, src = np.nonzero(off)
+    return from_arcs(n, dst, src, -V[dst, src]), V
+
+
 SEED_ER1000 = 20030245
 SEED_BATCH = 4096
 SEED_SERVE = 5150
@@ -223,6 +244,27 @@ def grid45(precision: str = "c64") -> WalkConfig:
     centre = 22 * 45 + 22
     return WalkConfig("grid45", g, 0.1, basis_state(2025, centre), 0.0, 0.5, 20,
                       precision=precision, note="2-D square lattice 45x45, N=2025")
+
+
+SEED_EST = 7440
+
+
+def est_dipole(count: int = 4, n: int = 10, omegas: int = 64, seed: int = SEED_EST,
+               t_end: float = 40.0, q: int = 400):
+    """Expected-survival-time sweep (Section 4.1.4): `count` dipole networks of
+    n points, each with a source (rate 0.5) feeding vertex 0 and a sink (rate
+    0.5) draining vertex n - 1, for omega = k / omegas, k = 1..omegas.  The
+    walker starts in the source vertex.  Returns a list of dicts (G, H, omega,
+    sources, sinks, rho0 as the source's basis state, sink index, t_end, q)."""
+    walks = []
+    for b in range(count):
+        g, h = dipole_network(n, seed * 31 + b)
+        nt = n + 2
+        for k in range(1, omegas + 1):
+            walks.append(dict(graph=g, H=h, omega=k / omegas, sources=[(0, 0.5)],
+                              sinks=[(n - 1, 0.5)], rho0=basis_state(nt, n), sink=n + 1,
+                              t_end=t_end, q=q, network=b))
+    return walks
 
 
 def batch_regular(count: int = 256, seed: int = SEED_BATCH, nmin: int = 16, nmax: int = 512,
