@@ -50,7 +50,10 @@ def parse_args():
                     help="skip the extra CSR-operator series measurement")
     ap.add_argument("--requests", type=int, default=2000, help="serve2000: number of requests")
     ap.add_argument("--walks", type=int, default=256, help="batch256: number of walks")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45"],
+    ap.add_argument("--est-networks", type=int, default=4, help="est: dipole networks")
+    ap.add_argument("--est-omegas", type=int, default=64, help="est: omega values per network")
+    ap.add_argument("--est-precision", default="c128", choices=["c128", "c64"], help="est: precision")
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45", "est"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -372,6 +375,87 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_est_workload(args):
+    """Expected-survival-time sweep (Section 4.1.4): `--est-networks` dipole
+    networks of 10 points uniform in the unit ball (V = -d^-3, source and sink of
+    rate 0.5), omega = k / `--est-omegas`, k = 1..; eta by Simpson over 600
+    intervals of [0, 300] (1 - p_sink(300) < 1e-6).  One step = build every
+    operator + one qsw_batch_survival_time launch (complex128).  The oracle times
+    one walk of the sweep as the CPU baseline."""
+    import numpy as np
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(0, stream.cuda_stream)
+    walks = W.est_dipole(count=args.est_networks, omegas=args.est_omegas, t_end=300.0, q=600)
+    rhos = [torch.from_numpy(W.vec(w["rho0"])).to(dev) for w in walks]
+
+    def step():
+        ops = [C.qsw_build_superoperator(ctx, w["graph"], w["H"], w["omega"], w["sources"],
+                                         w["sinks"], precision=args.est_precision, defer_norms=True)
+               for w in walks]
+        etas, st = C.qsw_batch_survival_time(ctx, ops, rhos, [w["t_end"] for w in walks],
+                                             [w["q"] for w in walks], [w["sink"] for w in walks])
+        for o in ops:
+            C.qsw_op_destroy(o)
+        return etas, st
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = C.qsw_kernel_launches()
+    ev0.record(stream)
+    res = [step() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    launches = (C.qsw_kernel_launches() - l0) / args.steps
+    etas, s0 = res[-1]
+    C.qsw_destroy(ctx)
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = est_cpu_baseline(walks, args.est_omegas)
+    line = {"metric": "expected survival times/s (dipole networks, omega sweep, batched)",
+            "value": len(walks) * 1000.0 / ms, "unit": "EST evaluations/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.est_precision, "data": "synthetic (seeded dipole networks in the unit ball)",
+            "config": {"workload": "est", "networks": args.est_networks, "points": 10,
+                       "omegas": args.est_omegas, "t_end": 300.0, "q": 600},
+            "batch": {"norms_ms": s0["norms_ms"], "series_ms": s0["series_ms"],
+                      "matvecs": s0["matvecs"], "clusters": s0["clusters"]},
+            "eta": {"min": float(np.min(etas)), "max": float(np.max(etas)),
+                    "first_network": [float(e) for e in etas[:args.est_omegas]]},
+            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
+    print(json.dumps(line))
+
+
+def est_cpu_baseline(walks, omegas):
+    """The oracle's survival time for one walk of each network (omega = 0.5),
+    single thread; the rate is walks / total time."""
+    import time
+    from oracle import est, graph, superop
+    from paper_2003_02450_gb300 import workloads as W
+    sample = [w for k, w in enumerate(walks) if k % omegas == omegas // 2 - 1]
+    t = time.perf_counter()
+    for w in sample:
+        walk = graph.lqsw_walk(graph.adjacency(w["graph"]), H=w["H"], sources=w["sources"],
+                               sinks=w["sinks"])
+        L = superop.superoperator(walk, w["omega"])
+        est.survival_time(L, walk.n_tilde, W.vec(w["rho0"]), w["t_end"], w["q"], w["sink"])
+    sec = time.perf_counter() - t
+    return {"value": len(sample) / sec, "unit": "EST evaluations/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(sample)} walks (one per network, omega={sample[0]['omega']:.3f}): "
+                      f"Kronecker superoperator + Algorithm 5.2 over 600 intervals + Simpson, "
+                      f"{sec:.1f} s"}
+
+
 def run_batch_workload(args):
     """256 random 4-regular walks (N ~ U{16..512}), omega ~ U(0,1), 4 random pure
     states each, 10 steps of dt = 0.2.  One step = build the 256 operators from
@@ -589,6 +673,9 @@ def main():
         return
     if args.workload == "grid45":
         run_grid_workload(args)
+        return
+    if args.workload == "est":
+        run_est_workload(args)
         return
     run_ours(args)
 

@@ -265,11 +265,15 @@ qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t
 /* Statistics of one qsw_batch_series call. */
 typedef struct {
   int32_t walks;        /* walks in the batch */
-  int32_t clusters;     /* thread-block clusters (8 CTAs each) resident */
+  int32_t clusters;     /* thread-block clusters (8 CTAs each) resident in the
+                           series phase (0: every walk was small) */
   double norms_ms;      /* device time of the 1-norm phase */
   double series_ms;     /* device time of the series phase */
   int64_t matvecs;      /* applications of the walks' L~ to an n x n0 block */
   int64_t fupdates;     /* sum over terms of the outputs updated */
+  int32_t small_walks;  /* walks whose two n x n0 Taylor-term blocks fit in
+                           64 KB: run by one thread block each with the terms
+                           in shared memory, alongside the clusters */
 } qsw_batch_stats;
 
 /* Many independent walks in one launch (not in the paper): walk w is `ops[w]`
@@ -288,6 +292,33 @@ qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,
                             const double* dt, const int32_t* steps, double* const* d_pops,
                             qsw_batch_stats* stats);
+
+/* ------------------------------------------- expected survival time */
+
+/* Expected survival time of a walk with a sink (Section 4.1.4, transport
+ * through a disordered network):
+ *   eta = integral over [0, t_end] of (1 - p_sink(t)),
+ * evaluated as the paper does: the series of populations at t_k = k h,
+ * h = t_end / q, k = 0..q (qsw_expmv_series from t0 = 0), then Simpson's rule
+ * h/3 (y_0 + 4 y_1 + 2 y_2 + ... + 4 y_{q-1} + y_q) on y_k = 1 - p_sink(t_k).
+ * `sink` is the vertex index of the sink (sinks follow the N graph vertices
+ * and the sources).  q must be even and >= 2; t_end finite and > 0.  *eta is
+ * a host double.  d_pops, when non-NULL, receives the (q+1) x N~ populations
+ * (device); otherwise the call uses its own workspace.  Synchronises the
+ * stream.  Errors: INVALID_ARG (odd q, bad sink, ...), OOM, NOT_CONVERGED,
+ * CUDA. */
+qsw_status qsw_survival_time(qsw_op* op, const double* d_rho0, double t_end, int32_t q,
+                             int32_t sink, double* eta, double* d_pops, qsw_series_stats* stats);
+
+/* The same for `count` walks in one batched launch (qsw_batch_series with
+ * n0 = 1, t0 = 0, dt = t_end[w] / q[w], steps = q[w]), e.g. a sweep of eta over
+ * omega.  t_end, q, sink and eta are host arrays of `count` entries; the
+ * populations live in the call's workspace.  Errors as qsw_batch_series, plus
+ * those of qsw_survival_time. */
+qsw_status qsw_batch_survival_time(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
+                                   const double* const* d_rho0, const double* t_end,
+                                   const int32_t* q, const int32_t* sink, double* eta,
+                                   qsw_batch_stats* stats);
 
 /* ------------------------------------------------------------- serving */
 

@@ -150,7 +150,10 @@ qsw_status qsw_create(qsw_ctx** out, int device, void* stream) {
   });
 }
 
-void qsw_destroy(qsw_ctx* ctx) { delete ctx; }
+void qsw_destroy(qsw_ctx* ctx) {
+  if (ctx && ctx->side) cudaStreamDestroy(ctx->side);
+  delete ctx;
+}
 
 const char* qsw_last_error(const qsw_ctx* ctx) {
   return ctx ? ctx->last_error.c_str() : g_orphan_error.c_str();
@@ -423,6 +426,35 @@ qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
     set_device(ctx);
     qsw::run_batch(ctx, count, reinterpret_cast<Op* const*>(ops), d_rho0, n0, t0, dt, steps,
                    d_pops, stats);
+  });
+}
+
+qsw_status qsw_survival_time(qsw_op* h, const double* d_rho0, double t_end, int32_t q,
+                             int32_t sink, double* eta, double* d_pops, qsw_series_stats* stats) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op && d_rho0 && eta, QSW_ERR_INVALID_ARG, "op/rho0/eta is NULL");
+    set_device(op->ctx);
+    ensure_norms(*op);
+    qsw::run_survival(*op, d_rho0, t_end, q, sink, eta, d_pops, stats);
+  });
+}
+
+qsw_status qsw_batch_survival_time(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
+                                   const double* const* d_rho0, const double* t_end,
+                                   const int32_t* q, const int32_t* sink, double* eta,
+                                   qsw_batch_stats* stats) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx && count >= 1 && ops && d_rho0 && t_end && q && sink && eta,
+                  QSW_ERR_INVALID_ARG, "bad arguments to qsw_batch_survival_time");
+    for (int w = 0; w < count; ++w) {
+      QSW_CHECK_ARG(ops[w] && d_rho0[w], QSW_ERR_INVALID_ARG, "NULL walk pointer");
+      QSW_CHECK_ARG(reinterpret_cast<Op*>(ops[w])->ctx == ctx, QSW_ERR_INVALID_ARG,
+                    "operator from another context");
+    }
+    set_device(ctx);
+    qsw::run_batch_survival(ctx, count, reinterpret_cast<Op* const*>(ops), d_rho0, t_end, q, sink,
+                            eta, stats);
   });
 }
 

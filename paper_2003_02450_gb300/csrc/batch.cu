@@ -17,12 +17,19 @@
 // block of n0 <= 4 right-hand sides (A-H treat B = [b_1 .. b_n0] as one matrix:
 // ||B||_inf is the largest row sum of moduli), populations of every output.
 // Hermitian right-hand sides are computed on upper triangles as in series.cu.
+//
+// Small walks (their two Taylor-term blocks fit in 64 KB) take phase 2 on ONE
+// CTA instead, with the Taylor terms in shared memory: for such walks each term
+// is a few hundred nanoseconds of work, and a cluster's barriers and its
+// gathers of terms written by other SMs (L2 round trips) would dominate.  The
+// small-walk kernel runs on a second stream alongside the cluster kernel.
 #include <cooperative_groups.h>
 #include <math.h>
 #include <string.h>
 
 #include <algorithm>
 #include <numeric>
+#include <type_traits>
 
 #include "matfree.cuh"
 #include "op.h"
@@ -73,6 +80,7 @@ struct BWalk {
   void* kbuf;          // 2 x n0 x n of VT
   double2* fring;      // ring x n0 x n
   int ring;
+  int fsmem;           // small walks: the ring lives in shared memory after the terms
   Job* jobs;
   int njobs;
   long long* counters; // [0] matvecs, [1] fupdates, [2] plan mismatch
@@ -80,11 +88,18 @@ struct BWalk {
 
 struct BArgs {
   BWalk* walks;
-  const int* order;    // walk indices, largest first
+  const int* order;    // phase 1: every walk, largest first
   int count;
-  unsigned int* queue; // [0] phase-1 counter, [1] phase-2 counter
+  const int* big;      // phase 2 on clusters: walks too large for one CTA, largest first
+  int nbig;
+  const int* small;    // phase 2 on one CTA each, largest first
+  int nsmall;
+  unsigned int* queue; // [0] phase 1, [1] cluster phase 2, [2] small-walk phase 2
   double tol[2];
 };
+
+constexpr size_t kSmallKBytes = 64 * 1024;       // two Taylor-term blocks of a small walk
+constexpr size_t kSmallTotalBytes = 96 * 1024;   // ... plus its output ring, when that fits
 
 __device__ __forceinline__ unsigned long long bits_of(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -109,6 +124,22 @@ struct Red {
   int blki[2];
   double out[2];
   int outi[2];
+};
+
+// The CTAs that share one walk in phase 2: a thread-block cluster (hardware
+// barrier, partial results read through distributed shared memory) or one CTA.
+struct ClusterG {
+  cg::cluster_group cl;
+  static constexpr int kSize = kCl;
+  __device__ int rank() const { return (int)cl.block_rank(); }
+  __device__ void sync() { cl.sync(); }
+  __device__ const Red* peer(Red& R, int r) { return cl.map_shared_rank(&R, r); }
+};
+struct CtaG {
+  static constexpr int kSize = 1;
+  __device__ int rank() const { return 0; }
+  __device__ void sync() { __syncthreads(); }
+  __device__ const Red* peer(Red& R, int) { return &R; }
 };
 
 __device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
@@ -148,35 +179,48 @@ __device__ void cl_sum2(cg::cluster_group& cl, Red& R, double a, double b, doubl
   ob = R.out[1];
 }
 
-// Max of two non-negative values over the cluster.
-__device__ void cl_max2(cg::cluster_group& cl, Red& R, double a, double b, double& oa, double& ob) {
+// Max of two non-negative values over the group's CTAs.  Non-negative doubles
+// order like their bit patterns, so the maxima are integer operations (the
+// FP64 pipe is 1/64 of FP32 on this part and is kept for the arithmetic).
+__device__ __forceinline__ double dmax_bits(double a, double b) {
+  return __longlong_as_double(max(__double_as_longlong(a), __double_as_longlong(b)));
+}
+
+template <class G>
+__device__ void grp_max2(G& g, Red& R, double a, double b, double& oa, double& ob) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int o = 16; o > 0; o >>= 1) {
-    a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
-    b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    a = dmax_bits(a, __shfl_xor_sync(0xffffffffu, a, o));
+    b = dmax_bits(b, __shfl_xor_sync(0xffffffffu, b, o));
   }
   if (lane == 0) { R.v[warp][0] = a; R.v[warp][1] = b; }
   __syncthreads();
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0;
-    for (int w = 0; w < kBW; ++w) { s0 = fmax(s0, R.v[w][0]); s1 = fmax(s1, R.v[w][1]); }
+    for (int w = 0; w < kBW; ++w) { s0 = dmax_bits(s0, R.v[w][0]); s1 = dmax_bits(s1, R.v[w][1]); }
     R.blk[0] = s0;
     R.blk[1] = s1;
   }
-  cl.sync();
+  g.sync();
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0;
-    for (int r = 0; r < kCl; ++r) {
-      const Red* p = cl.map_shared_rank(&R, r);
-      s0 = fmax(s0, p->blk[0]);
-      s1 = fmax(s1, p->blk[1]);
+    for (int r = 0; r < G::kSize; ++r) {
+      const Red* p = g.peer(R, r);
+      s0 = dmax_bits(s0, p->blk[0]);
+      s1 = dmax_bits(s1, p->blk[1]);
     }
     R.out[0] = s0;
     R.out[1] = s1;
   }
-  cl.sync();
+  g.sync();
   oa = R.out[0];
   ob = R.out[1];
+}
+
+__device__ __forceinline__ void cl_max2(cg::cluster_group& cl, Red& R, double a, double b,
+                                        double& oa, double& ob) {
+  ClusterG g{cl};
+  grp_max2(g, R, a, b, oa, ob);
 }
 
 // argmax over the cluster: larger value first, ties to the smaller index.
@@ -214,10 +258,11 @@ __device__ void cl_argmax(cg::cluster_group& cl, Red& R, double v, int i, double
 }
 
 // Next walk from the queue (cluster rank 0 takes it, everyone reads it).
-__device__ int next_walk(cg::cluster_group& cl, unsigned int* counter, int* s_w, const BArgs& a) {
+__device__ int next_walk(cg::cluster_group& cl, unsigned int* counter, int* s_w,
+                          const int* list, int count) {
   if (cl.block_rank() == 0 && threadIdx.x == 0) {
     const unsigned k = atomicAdd(counter, 1u);
-    *s_w = k < (unsigned)a.count ? a.order[k] : -1;
+    *s_w = k < (unsigned)count ? list[k] : -1;
   }
   cl.sync();
   const int w = *cl.map_shared_rank(s_w, 0);
@@ -265,7 +310,7 @@ batch_norms_kernel(BArgs a) {
   const long long ct = (long long)crank * kBT + threadIdx.x;   // thread index in the cluster
   const long long cstride = (long long)kCl * kBT;
   for (;;) {
-    const int wi = next_walk(cl, &a.queue[0], &s_w, a);
+    const int wi = next_walk(cl, &a.queue[0], &s_w, a.order, a.count);
     if (wi < 0) break;
     BWalk& W = a.walks[wi];
     const int Nt = W.Nt;
@@ -475,23 +520,37 @@ template <int N0> struct NormAcc<false, N0> {
 
 constexpr int kBKReg = 4;   // outputs whose running maxima live in registers
 
-template <class VT, int N0>
-__device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk& W, double tol, double* s_coef,
-                         double* s_step, double* s_c1, int* s_active) {
+// Reads of the output ring and of Z: global-memory reads that bypass L1 on a
+// cluster (other CTAs wrote them), generic reads in one-CTA mode (the ring may
+// be in shared memory; in global memory this CTA wrote it itself).
+template <bool SK> __device__ __forceinline__ double2 ldf(const double2* p) {
+  if (SK) return *p;
+  return __ldcg(p);
+}
+
+// Phase 2 of one walk on group g.  SK: the Taylor-term blocks live in shared
+// memory at `sk` (one-CTA groups); otherwise in the walk's workspace.
+template <class G, class VT, int N0, bool SK>
+__device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, double* s_coef,
+                                      double* s_step, double* s_c1, int* s_active, VT* sk) {
   using Rt = typename BC<VT>::R;
   constexpr bool kF32 = sizeof(Rt) == sizeof(float);
   using NA = NormAcc<kF32, N0>;
   using NT = typename NA::T;
-  const int crank = (int)cl.block_rank();
+  using LDP = typename std::conditional<SK, LdGeneric, LdGlobal>::type;
+  const int crank = g.rank();
   const long long ct = (long long)crank * kBT + threadIdx.x;
-  const long long cstride = (long long)kCl * kBT;
+  const long long cstride = (long long)G::kSize * kBT;
   const int Nt = W.Nt;
   const long long n = W.n;
   const bool herm = W.herm != 0;
   const MfOp<Rt>& op = BC<VT>::mf(W);
   const int lane = threadIdx.x & 31;
   const int gw = crank * kBW + (threadIdx.x >> 5);
-  double2* const fring = W.fring;
+  // outputs: the walk's ring in global memory, or (small walks whose ring fits)
+  // in shared memory right after the two Taylor-term blocks
+  double2* const fring =
+      (SK && W.fsmem) ? reinterpret_cast<double2*>(sk + 2 * (long long)N0 * n) : W.fring;
   const int ring = W.ring;
   auto fslot = [&](int idx) { return fring + (long long)(idx % ring) * N0 * n; };
   // per-block maxima of outputs k >= kBKReg (shared, as bit patterns)
@@ -501,7 +560,7 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
   for (int jb = 0; jb < W.njobs; ++jb) {
     const Job J = W.jobs[jb];
     const double2* Z = J.z_slot < 0 ? W.rho0 : fslot(J.z_slot);
-    VT* kc = static_cast<VT*>(W.kbuf);
+    VT* kc = SK ? sk : static_cast<VT*>(W.kbuf);
     VT* kn = kc + (long long)N0 * n;
     // init: Khat_0 = Z, F_k = Z, ||Z||_inf
     NT zn = 0;
@@ -512,10 +571,10 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
       for (int c = 0; c < N0; ++c) {
         double2 z;
         if (herm && i > j) {
-          z = __ldcg(Z + c * n + j + (long long)Nt * i);
+          z = ldf<SK>(Z + c * n + j + (long long)Nt * i);
           z.y = -z.y;
         } else {
-          z = __ldcg(Z + c * n + r);
+          z = ldf<SK>(Z + c * n + r);
         }
         kc[c * n + r] = BC<VT>::mk((Rt)z.x, (Rt)z.y);
         for (int k = 0; k < J.d; ++k) fslot(J.out_index0 + k)[c * n + r] = z;
@@ -524,7 +583,7 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
       zn = NA::vmax(zn, rs);
     }
     double znorm, dmy;
-    cl_max2(cl, R, (double)zn, 0.0, znorm, dmy);
+    grp_max2(g, R, (double)zn, 0.0, znorm, dmy);
     if (N0 == 1) znorm = sqrt(znorm);
     for (int k = threadIdx.x; k < J.d; k += kBT) {
       s_c1[k] = znorm;
@@ -535,9 +594,12 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
     }
     __syncthreads();
     for (int p = 1; p <= J.m; ++p) {
-      const Rt scale = (Rt)(J.hspan / p);
+      // h/p once per CTA (an FP64 division is a long FP64-pipe sequence)
+      __shared__ double s_scale;
+      if (threadIdx.x == 0) s_scale = J.hspan / p;
       for (int k = threadIdx.x; k < J.d; k += kBT) s_coef[k] *= s_step[k];
       __syncthreads();
+      const Rt scale = (Rt)s_scale;
       double coef[kBKReg];
       bool own[kBKReg];
 #pragma unroll
@@ -549,105 +611,135 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
       NT fmx[kBKReg];
 #pragma unroll
       for (int u = 0; u < kBKReg; ++u) fmx[u] = 0;
-      const long long nitems = mf_item_count(Nt, herm);
-      for (long long it = gw; it < nitems; it += kCl * kBW) {
-        int j, i0;
-        mf_item(it, Nt, herm, j, i0);
-        int irow[2];
-#pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          const int i = i0 + lane + 32 * u;
-          irow[u] = (i < Nt && (!herm || i <= j)) ? i : -1;
-        }
-        Rt yx[2][N0], yy[2][N0];
+      // the new term at element (i, j) (all n0 columns): store it (and its
+      // mirror), fold it into the running maxima and the active outputs
+      auto element = [&](int i, int j, const Rt* yx, const Rt* yy) {
+        const long long r = i + (long long)Nt * j;
+        NT rs = 0;
+        double dx[N0], dy[N0];
 #pragma unroll
         for (int c = 0; c < N0; ++c) {
-          Rt cx[2], cy[2];
-          mf_partB<Rt, VT, 2>(op, kc + c * n, j, irow, cx, cy);
-#pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            yx[u][c] = 0;
-            yy[u][c] = 0;
-            if (irow[u] >= 0)
-              mf_finish<Rt, VT, false>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c], yy[u][c]);
-          }
+          const Rt ax = yx[c] * scale, ay = yy[c] * scale;
+          kn[c * n + r] = BC<VT>::mk(ax, ay);
+          if (herm && i != j) kn[c * n + j + (long long)Nt * i] = BC<VT>::mk(ax, -ay);
+          rs += NA::of_f((NT)ax, (NT)ay);
+          dx[c] = (double)ax;
+          dy[c] = (double)ay;
         }
+        kmax = NA::vmax(kmax, rs);
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-          if (irow[u] < 0) continue;
-          const int i = irow[u];
-          const long long r = i + (long long)Nt * j;
-          NT rs = 0;
-          double dx[N0], dy[N0];
+        for (int u2 = 0; u2 < kBKReg; ++u2) {
+          if (!own[u2]) continue;
+          double2* F = fslot(J.out_index0 + u2);
+          NT fs = 0;
 #pragma unroll
           for (int c = 0; c < N0; ++c) {
-            const Rt ax = yx[u][c] * scale, ay = yy[u][c] * scale;
-            kn[c * n + r] = BC<VT>::mk(ax, ay);
-            if (herm && i != j) kn[c * n + j + (long long)Nt * i] = BC<VT>::mk(ax, -ay);
-            rs += NA::of_f((NT)ax, (NT)ay);
-            dx[c] = (double)ax;
-            dy[c] = (double)ay;
+            double2 f = ldf<SK>(F + c * n + r);
+            f.x = fma(coef[u2], dx[c], f.x);
+            f.y = fma(coef[u2], dy[c], f.y);
+            F[c * n + r] = f;
+            fs += NA::of(f.x, f.y);
           }
-          kmax = NA::vmax(kmax, rs);
+          fmx[u2] = NA::vmax(fmx[u2], fs);
+        }
+        for (int k = kBKReg; k < J.d; ++k) {
+          if (!s_active[k]) continue;
+          const double ck = s_coef[k];
+          double2* F = fslot(J.out_index0 + k);
+          NT fs = 0;
 #pragma unroll
-          for (int u2 = 0; u2 < kBKReg; ++u2) {
-            if (!own[u2]) continue;
-            double2* F = fslot(J.out_index0 + u2);
-            NT fs = 0;
+          for (int c = 0; c < N0; ++c) {
+            double2 f = ldf<SK>(F + c * n + r);
+            f.x = fma(ck, dx[c], f.x);
+            f.y = fma(ck, dy[c], f.y);
+            F[c * n + r] = f;
+            fs += NA::of(f.x, f.y);
+          }
+          atomicMax(&s_extra[k], bits_of((double)fs));
+        }
+      };
+      if (SK) {
+        // one CTA, terms on chip: one thread per element (upper triangle in
+        // the Hermitian form), so a small walk's rows fill the warps
+        const long long nel = herm ? (long long)Nt * (Nt + 1) / 2 : n;
+        for (long long q = threadIdx.x; q < nel; q += kBT) {
+          int i, j;
+          if (herm) {
+            j = (int)((sqrtf(8.0f * (float)q + 1.0f) - 1.0f) * 0.5f);
+            while ((long long)j * (j + 1) / 2 > q) --j;
+            while ((long long)(j + 1) * (j + 2) / 2 <= q) ++j;
+            i = (int)(q - (long long)j * (j + 1) / 2);
+          } else {
+            i = (int)(q % Nt);
+            j = (int)(q / Nt);
+          }
+          Rt yx[N0], yy[N0];
 #pragma unroll
-            for (int c = 0; c < N0; ++c) {
-              double2 f = __ldcg(F + c * n + r);
-              f.x = fma(coef[u2], dx[c], f.x);
-              f.y = fma(coef[u2], dy[c], f.y);
-              F[c * n + r] = f;
-              fs += NA::of(f.x, f.y);
+          for (int c = 0; c < N0; ++c) {
+            Rt cx, cy;
+            mf_partB<Rt, VT, 1, LDP>(op, kc + c * n, j, &i, &cx, &cy);
+            mf_finish<Rt, VT, false, LDP>(op, kc + c * n, i, j, cx, cy, yx[c], yy[c]);
+          }
+          element(i, j, yx, yy);
+        }
+      } else {
+        const long long nitems = mf_item_count(Nt, herm);
+        for (long long it = gw; it < nitems; it += G::kSize * kBW) {
+          int j, i0;
+          mf_item(it, Nt, herm, j, i0);
+          int irow[2];
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            const int i = i0 + lane + 32 * u;
+            irow[u] = (i < Nt && (!herm || i <= j)) ? i : -1;
+          }
+          Rt yx[2][N0], yy[2][N0];
+#pragma unroll
+          for (int c = 0; c < N0; ++c) {
+            Rt cx[2], cy[2];
+            mf_partB<Rt, VT, 2, LDP>(op, kc + c * n, j, irow, cx, cy);
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              yx[u][c] = 0;
+              yy[u][c] = 0;
+              if (irow[u] >= 0)
+                mf_finish<Rt, VT, false, LDP>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c],
+                                              yy[u][c]);
             }
-            fmx[u2] = NA::vmax(fmx[u2], fs);
           }
-          for (int k = kBKReg; k < J.d; ++k) {
-            if (!s_active[k]) continue;
-            const double ck = s_coef[k];
-            double2* F = fslot(J.out_index0 + k);
-            NT fs = 0;
 #pragma unroll
-            for (int c = 0; c < N0; ++c) {
-              double2 f = __ldcg(F + c * n + r);
-              f.x = fma(ck, dx[c], f.x);
-              f.y = fma(ck, dy[c], f.y);
-              F[c * n + r] = f;
-              fs += NA::of(f.x, f.y);
-            }
-            atomicMax(&s_extra[k], bits_of((double)fs));
-          }
+          for (int u = 0; u < 2; ++u)
+            if (irow[u] >= 0) element(irow[u], j, yx[u], yy[u]);
         }
       }
       // cluster maxima: K and the register outputs in pairs, the rest from s_extra
       double fn[kBDMax];
       double gk;
-      cl_max2(cl, R, (double)kmax, (double)fmx[0], gk, fn[0]);
+      grp_max2(g, R, (double)kmax, (double)fmx[0], gk, fn[0]);
 #pragma unroll
       for (int u = 1; u < kBKReg; u += 2) {
         if (u >= J.d) break;
         double a0, a1;
-        cl_max2(cl, R, (double)fmx[u], u + 1 < kBKReg ? (double)fmx[u + 1] : 0.0, a0, a1);
+        grp_max2(g, R, (double)fmx[u], u + 1 < kBKReg ? (double)fmx[u + 1] : 0.0, a0, a1);
         fn[u] = a0;
         if (u + 1 < kBKReg) fn[u + 1] = a1;
       }
       for (int k = kBKReg; k < J.d; k += 2) {
         double a0, a1;
-        cl_max2(cl, R, of_bits(s_extra[k]), k + 1 < J.d ? of_bits(s_extra[k + 1]) : 0.0, a0, a1);
+        grp_max2(g, R, of_bits(s_extra[k]), k + 1 < J.d ? of_bits(s_extra[k + 1]) : 0.0, a0, a1);
         fn[k] = a0;
         if (k + 1 < J.d) fn[k + 1] = a1;
       }
       ++matvecs;
       for (int k = 0; k < J.d; ++k) fupd += s_active[k];
-      const double normk = N0 == 1 ? sqrt(gk) : gk;
-      // stop test, identical in every CTA of the cluster
+      // stop test, identical in every CTA of the cluster (only the threads
+      // that own an output take the square roots)
       int any = 0;
       __syncthreads();
       for (int k = threadIdx.x; k < J.d; k += kBT) {
         s_extra[k] = 0ULL;
         if (!s_active[k]) continue;
+        const double normk = N0 == 1 ? sqrt(gk) : gk;
         const double c2 = s_coef[k] * normk;
         const double nf = N0 == 1 ? sqrt(fn[k]) : fn[k];
         if (s_c1[k] + c2 <= tol * nf) s_active[k] = 0;
@@ -667,15 +759,32 @@ __device__ __noinline__ void run_walk(cg::cluster_group& cl, Red& R, const BWalk
         const int k = (int)(q / ((long long)N0 * Nt));
         const int rem = (int)(q % ((long long)N0 * Nt));
         const int c = rem / Nt, v = rem % Nt;
-        const double2 z = __ldcg(fslot(J.out_index0 + k) + c * n + (long long)v * (Nt + 1));
+        const double2 z = ldf<SK>(fslot(J.out_index0 + k) + c * n + (long long)v * (Nt + 1));
         W.pops[((long long)(J.out_index0 + k) * N0 + c) * Nt + v] = z.x;
       }
     }
-    cl.sync();   // outputs complete before the next block reads them
+    g.sync();   // outputs complete before the next block reads them
   }
   if (crank == 0 && threadIdx.x == 0) {
     W.counters[0] = matvecs;
     W.counters[1] = fupd;
+  }
+}
+
+template <class G, bool SK>
+__device__ void dispatch_walk(G g, Red& R, const BWalk& W, double tol, double* s_coef,
+                              double* s_step, double* s_c1, int* s_active, unsigned char* sk) {
+  double2* kd = reinterpret_cast<double2*>(sk);
+  float2* kf = reinterpret_cast<float2*>(sk);
+  switch (W.n0 * 2 + W.f32) {
+    case 2: run_walk<G, double2, 1, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kd); break;
+    case 3: run_walk<G, float2, 1, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kf); break;
+    case 4: run_walk<G, double2, 2, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kd); break;
+    case 5: run_walk<G, float2, 2, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kf); break;
+    case 6: run_walk<G, double2, 3, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kd); break;
+    case 7: run_walk<G, float2, 3, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kf); break;
+    case 8: run_walk<G, double2, 4, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kd); break;
+    default: run_walk<G, float2, 4, SK>(g, R, W, tol, s_coef, s_step, s_c1, s_active, kf); break;
   }
 }
 
@@ -691,7 +800,7 @@ batch_series_kernel(BArgs a) {
   for (int k = threadIdx.x; k < 2 * kBDMax; k += kBT) s_c1[k] = 0.0;
   __syncthreads();
   for (;;) {
-    const int wi = next_walk(cl, &a.queue[1], &s_w, a);
+    const int wi = next_walk(cl, &a.queue[1], &s_w, a.big, a.nbig);
     if (wi < 0) break;
     BWalk& W = a.walks[wi];
     // plan on the device from the walk's own norms
@@ -703,16 +812,41 @@ batch_series_kernel(BArgs a) {
     cl.sync();
     if (__ldcg(&W.counters[2])) continue;   // L2 read: every CTA sees rank 0's flag
     const double tol = a.tol[W.f32 ? 1 : 0];
-    switch (W.n0 * 2 + W.f32) {
-      case 2: run_walk<double2, 1>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 3: run_walk<float2, 1>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 4: run_walk<double2, 2>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 5: run_walk<float2, 2>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 6: run_walk<double2, 3>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 7: run_walk<float2, 3>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      case 8: run_walk<double2, 4>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
-      default: run_walk<float2, 4>(cl, R, W, tol, s_coef, s_step, s_c1, s_active); break;
+    dispatch_walk<ClusterG, false>(ClusterG{cl}, R, W, tol, s_coef, s_step, s_c1, s_active,
+                                   nullptr);
+  }
+}
+
+// Phase 2 for small walks: one CTA per walk, Taylor terms in dynamic shared
+// memory (2 n0 n values of the walk's precision, at most kSmallKBytes).
+__global__ void __launch_bounds__(kBT) batch_small_kernel(BArgs a) {
+  extern __shared__ __align__(16) unsigned char s_k[];
+  __shared__ Red R;
+  __shared__ int s_w;
+  __shared__ double s_coef[kBDMax];
+  __shared__ double s_step[kBDMax];
+  __shared__ double s_c1[2 * kBDMax];
+  __shared__ int s_active[kBDMax];
+  for (int k = threadIdx.x; k < 2 * kBDMax; k += kBT) s_c1[k] = 0.0;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned k = atomicAdd(&a.queue[2], 1u);
+      s_w = k < (unsigned)a.nsmall ? a.small[k] : -1;
     }
+    __syncthreads();
+    const int wi = s_w;
+    __syncthreads();
+    if (wi < 0) break;
+    BWalk& W = a.walks[wi];
+    if (threadIdx.x == 0) {
+      const PlanInfo info = plan_series(W.dp, c_theta_b[W.f32 ? 1 : 0], W.t0, W.dt, W.steps, W.n0,
+                                        W.ring, W.jobs, W.njobs);
+      if (info.njobs != W.njobs || info.max_d > kBDMax) W.counters[2] = 1;
+    }
+    __syncthreads();
+    if (*((volatile long long*)&W.counters[2])) continue;
+    const double tol = a.tol[W.f32 ? 1 : 0];
+    dispatch_walk<CtaG, true>(CtaG{}, R, W, tol, s_coef, s_step, s_c1, s_active, s_k);
   }
 }
 
@@ -802,11 +936,11 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return hw[x].n > hw[y].n; });
   DevBuf dwalks, dorder, dq;
   dwalks.alloc(sizeof(BWalk) * count);
-  dorder.alloc(sizeof(int) * count);
-  dq.alloc(sizeof(unsigned) * 2);
+  dorder.alloc(sizeof(int) * 3 * count);   // phase-1 order, cluster list, small list
+  dq.alloc(sizeof(unsigned) * 3);
   QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice, st));
   QSW_CUDA_TRY(cudaMemcpyAsync(dorder.p, order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st));
-  QSW_CUDA_TRY(cudaMemsetAsync(dq.p, 0, sizeof(unsigned) * 2, st));
+  QSW_CUDA_TRY(cudaMemsetAsync(dq.p, 0, sizeof(unsigned) * 3, st));
   BArgs args{};
   args.walks = dwalks.as<BWalk>();
   args.order = dorder.as<int>();
@@ -836,6 +970,8 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   QSW_CUDA_TRY(cudaMemcpyAsync(dps.data(), dpbuf.p, sizeof(double) * dps.size(),
                                cudaMemcpyDeviceToHost, st));
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  std::vector<char> is_small(count, 0);
+  std::vector<size_t> smem_of(count, 0);
   for (int w = 0; w < count; ++w) {
     BWalk& W = hw[w];
     const double* theta = theta_table(W.f32 ? QSW_C64_BULK : QSW_C128);
@@ -846,19 +982,73 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     W.njobs = info.njobs;
     W.ring = info.max_d + 1;
     const size_t vb = W.f32 ? sizeof(float2) : sizeof(double2);
-    bufs.emplace_back();
-    bufs.back().alloc(2 * vb * n0 * (size_t)W.n);
-    W.kbuf = bufs.back().p;
-    bufs.emplace_back();
-    bufs.back().alloc(sizeof(double2) * (size_t)W.ring * n0 * W.n);
-    W.fring = bufs.back().as<double2>();
+    const size_t kb = 2 * vb * n0 * (size_t)W.n;
+    const size_t rb = sizeof(double2) * (size_t)W.ring * n0 * W.n;
+    is_small[w] = kb <= kSmallKBytes;
+    W.fsmem = is_small[w] && kb + rb <= kSmallTotalBytes;
+    smem_of[w] = kb + (W.fsmem ? rb : 0);
+    if (!is_small[w]) {   // small walks keep their Taylor terms in shared memory
+      bufs.emplace_back();
+      bufs.back().alloc(2 * vb * n0 * (size_t)W.n);
+      W.kbuf = bufs.back().p;
+    }
+    if (!W.fsmem) {
+      bufs.emplace_back();
+      bufs.back().alloc(rb);
+      W.fring = bufs.back().as<double2>();
+    }
     bufs.emplace_back();
     bufs.back().alloc(sizeof(Job) * std::max(1, W.njobs));
     W.jobs = bufs.back().as<Job>();
   }
+  std::vector<int> big, small;
+  size_t small_bytes = 0;
+  for (int w : order) {
+    if (is_small[w]) {
+      small.push_back(w);
+      small_bytes = std::max(small_bytes, smem_of[w]);
+    } else {
+      big.push_back(w);
+    }
+  }
   QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice, st));
-  QSW_LAUNCH batch_series_kernel<<<clusters * kCl, kBT, 0, st>>>(args);
-  QSW_CUDA_TRY(cudaGetLastError());
+  std::vector<int> lists(big);
+  lists.insert(lists.end(), small.begin(), small.end());
+  if (!lists.empty())
+    QSW_CUDA_TRY(cudaMemcpyAsync(dorder.as<int>() + count, lists.data(), sizeof(int) * lists.size(),
+                                 cudaMemcpyHostToDevice, st));
+  args.big = dorder.as<int>() + count;
+  args.nbig = (int)big.size();
+  args.small = args.big + big.size();
+  args.nsmall = (int)small.size();
+  const int clusters2 = std::max(1, std::min(max_clusters, (int)big.size()));
+  // small walks: one CTA each on the side stream, alongside the clusters
+  cudaEvent_t fork = nullptr, join = nullptr;
+  if (!small.empty()) {
+    const int dyn = (int)small_bytes;
+    QSW_CUDA_TRY(cudaFuncSetAttribute(batch_small_kernel,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    int per_sm = 0;
+    QSW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_small_kernel, kBT, dyn));
+    const int grid = std::max(1, std::min((int)small.size(), std::max(1, per_sm) * ctx->num_sms));
+    cudaStream_t ss = st;
+    if (!big.empty()) {
+      if (!ctx->side) QSW_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      QSW_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      QSW_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+      QSW_CUDA_TRY(cudaEventRecord(fork, st));
+      QSW_CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0));
+      ss = ctx->side;
+    }
+    QSW_LAUNCH batch_small_kernel<<<grid, kBT, dyn, ss>>>(args);
+    QSW_CUDA_TRY(cudaGetLastError());
+    if (join) QSW_CUDA_TRY(cudaEventRecord(join, ss));
+  }
+  if (!big.empty()) {
+    QSW_LAUNCH batch_series_kernel<<<clusters2 * kCl, kBT, 0, st>>>(args);
+    QSW_CUDA_TRY(cudaGetLastError());
+  }
+  if (join) QSW_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
   QSW_CUDA_TRY(cudaEventRecord(e2, st));
   std::vector<long long> hc(4 * count);
   QSW_CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt.p, cnt.bytes, cudaMemcpyDeviceToHost, st));
@@ -869,11 +1059,14 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaEventDestroy(e2);
+  if (fork) cudaEventDestroy(fork);
+  if (join) cudaEventDestroy(join);
   for (int w = 0; w < count; ++w)
     QSW_CHECK_ARG(hc[4 * w + 2] == 0, QSW_ERR_CUDA, "batched series: device plan mismatch");
   if (stats) {
     stats->walks = count;
-    stats->clusters = clusters;
+    stats->clusters = big.empty() ? 0 : clusters2;
+    stats->small_walks = (int)small.size();
     stats->norms_ms = ms1;
     stats->series_ms = ms2;
     long long mv = 0, fu = 0;

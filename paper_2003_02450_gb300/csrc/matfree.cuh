@@ -49,9 +49,19 @@ template <class T> __device__ __forceinline__ T ldcg_t(const T* p) { return __ld
 // about 20 times per element, which L1 serves instead of L2.
 template <class VT> __device__ __forceinline__ VT ldx(const VT* p) { return __ldca(p); }
 
+// Load policies of the helpers below: x in global memory (ldx), or x at a
+// generic address that may be shared memory (the small-walk batched kernel
+// keeps a walk's Taylor terms on chip).
+struct LdGlobal {
+  template <class VT> __device__ __forceinline__ static VT ld(const VT* p) { return ldx(p); }
+};
+struct LdGeneric {
+  template <class VT> __device__ __forceinline__ static VT ld(const VT* p) { return *p; }
+};
+
 // Part B of C for RPT rows of one column, accumulated with a minus sign:
 // c = -sum_{m in H row j} c_mj x_(i,m)  (the uniform list, coalesced over i).
-template <class R, class VT, int RPT>
+template <class R, class VT, int RPT, class LD = LdGlobal>
 __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict__ x, int j,
                                          const int* irow, R* cx, R* cy) {
 #pragma unroll
@@ -65,7 +75,7 @@ __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       if (irow[u] >= 0) {
-        const VT v = ldx(x + off + irow[u]);
+        const VT v = LD::ld(x + off + irow[u]);
         cx[u] = fma(-h, v.x, cx[u]);
         cy[u] = fma(-h, v.y, cy[u]);
       }
@@ -79,7 +89,7 @@ __device__ __forceinline__ void mf_partB(const MfOp<R>& op, const VT* __restrict
 // trip count is len(a) + len(b); the windows pair short rows with long ones
 // (mf_window_rows) to make that sum nearly equal across a warp.  Each row's
 // terms are added in the same order as a loop over that row alone.
-template <class R, class VT>
+template <class R, class VT, class LD = LdGlobal>
 __device__ __forceinline__ void mf_partA2(const MfOp<R>& op, const VT* __restrict__ x, int j,
                                           const int* irow, R* cx, R* cy) {
   const long long base = (long long)op.Nt * j;
@@ -93,7 +103,7 @@ __device__ __forceinline__ void mf_partA2(const MfOp<R>& op, const VT* __restric
   for (int t = 0; t < tot; ++t) {
     const bool second = t >= la;
     const int e = second ? eb + (t - la) : ea + t;
-    const VT v = ldx(x + base + op.hcol[e]);
+    const VT v = LD::ld(x + base + op.hcol[e]);
     const R h = op.hval[e];
     const R tx = fma(h, v.x, second ? bx : ax);
     const R ty = fma(h, v.y, second ? by : ay);
@@ -110,11 +120,11 @@ __device__ __forceinline__ void mf_partA2(const MfOp<R>& op, const VT* __restric
 
 // Element (i, j) once C is complete: the diagonal and the jumps; returns
 // (L x)_(i,j) or (L^H x)_(i,j).
-template <class R, class VT, bool ADJ>
+template <class R, class VT, bool ADJ, class LD = LdGlobal>
 __device__ __forceinline__ void mf_tail(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
                                         R cx, R cy, R& yx, R& yy) {
   const long long base = (long long)op.Nt * j;
-  const VT xs = ldx(x + base + i);
+  const VT xs = LD::ld(x + base + i);
   const R dx = op.ad[i] + op.ad[j];
   const R dy = op.hw[j] - op.hw[i];
   R rx, ry;
@@ -128,7 +138,7 @@ __device__ __forceinline__ void mf_tail(const MfOp<R>& op, const VT* __restrict_
   if (i == j) {
     const int e0 = op.jrow[i], e1 = op.jrow[i + 1];
     for (int e = e0; e < e1; ++e) {
-      const VT v = ldx(x + (long long)op.jcol[e] * (op.Nt + 1));
+      const VT v = LD::ld(x + (long long)op.jcol[e] * (op.Nt + 1));
       const R r = op.jval[e];
       rx = fma(r, v.x, rx);
       ry = fma(r, v.y, ry);
@@ -140,20 +150,20 @@ __device__ __forceinline__ void mf_tail(const MfOp<R>& op, const VT* __restrict_
 
 // The rest of element (i, j): part A (added to the same accumulators), the
 // diagonal and the jumps; returns (L x)_(i,j) or (L^H x)_(i,j).
-template <class R, class VT, bool ADJ>
+template <class R, class VT, bool ADJ, class LD = LdGlobal>
 __device__ __forceinline__ void mf_finish(const MfOp<R>& op, const VT* __restrict__ x, int i, int j,
                                           R cx, R cy, R& yx, R& yy) {
   const long long base = (long long)op.Nt * j;
   if (i < op.N) {
     const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
     for (int e = e0; e < e1; ++e) {
-      const VT v = ldx(x + base + op.hcol[e]);
+      const VT v = LD::ld(x + base + op.hcol[e]);
       const R h = op.hval[e];
       cx = fma(h, v.x, cx);
       cy = fma(h, v.y, cy);
     }
   }
-  mf_tail<R, VT, ADJ>(op, x, i, j, cx, cy, yx, yy);
+  mf_tail<R, VT, ADJ, LD>(op, x, i, j, cx, cy, yx, yy);
 }
 
 // Rows of one 64-row window for a lane: (prow[w0 + lane], prow[w0 + 32 + lane]),
@@ -179,20 +189,20 @@ constexpr int kItemRows = 64;
 // C for the two rows of one lane in window w0 of column j, then the element
 // values y = (L x) or (L^H x) (scaled by the caller): part B (uniform), part A
 // (merged over the pair when the window is paired), the diagonal and jumps.
-template <class R, class VT, bool ADJ>
+template <class R, class VT, bool ADJ, class LD = LdGlobal>
 __device__ __forceinline__ void mf_window_apply(const MfOp<R>& op, const VT* __restrict__ x, int j,
                                                 int w0, const int* irow, R* yx, R* yy) {
   R cx[2], cy[2];
-  mf_partB<R, VT, 2>(op, x, j, irow, cx, cy);
+  mf_partB<R, VT, 2, LD>(op, x, j, irow, cx, cy);
   if (op.pwin[w0 / kItemRows]) {
-    mf_partA2<R, VT>(op, x, j, irow, cx, cy);
+    mf_partA2<R, VT, LD>(op, x, j, irow, cx, cy);
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-      if (irow[u] >= 0) mf_tail<R, VT, ADJ>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
+      if (irow[u] >= 0) mf_tail<R, VT, ADJ, LD>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
   } else {
 #pragma unroll
     for (int u = 0; u < 2; ++u)
-      if (irow[u] >= 0) mf_finish<R, VT, ADJ>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
+      if (irow[u] >= 0) mf_finish<R, VT, ADJ, LD>(op, x, irow[u], j, cx[u], cy[u], yx[u], yy[u]);
   }
 }
 

@@ -6,6 +6,7 @@
 struct qsw_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;   // owned: the batched small-walk kernel's stream
   int num_sms = 0;
   std::string last_error;
 };
@@ -107,6 +108,12 @@ int choose_tpr(double avg_row);
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,
                qsw_batch_stats* stats);
+// est.cu
+void run_survival(Op& op, const double* d_rho0, double t_end, int q, int sink, double* eta,
+                  double* d_pops, qsw_series_stats* stats);
+void run_batch_survival(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0,
+                        const double* t_end, const int* q, const int* sink, double* eta,
+                        qsw_batch_stats* stats);
 
 inline unsigned grid_for(int64_t items, int block, int max_blocks = 1 << 20) {
   int64_t b = (items + block - 1) / block;

@@ -62,7 +62,8 @@ class qsw_series_stats(ctypes.Structure):
 
 class qsw_batch_stats(ctypes.Structure):
     _fields_ = [("walks", c_int32), ("clusters", c_int32), ("norms_ms", c_double),
-                ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64)]
+                ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64),
+                ("small_walks", c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -109,6 +110,11 @@ _SIGNATURES = {
     "qsw_expmv_series_host": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p,
                                c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
+    "qsw_survival_time": ([c_void_p, c_void_p, c_double, c_int32, c_int32, POINTER(c_double),
+                           c_void_p, POINTER(qsw_series_stats)], c_int32),
+    "qsw_batch_survival_time": ([c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p),
+                                 POINTER(c_double), POINTER(c_int32), POINTER(c_int32),
+                                 POINTER(c_double), POINTER(qsw_batch_stats)], c_int32),
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
     "qsw_kernel_launches": ([], c_int64),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
@@ -297,6 +303,30 @@ def qsw_batch_series(ctx, ops, d_rho0s, n0: int, t0s, dts, steps, d_pops) -> dic
                                   arr(c_int32, [int(x) for x in steps]),
                                   arr(c_void_p, [_ptr(x).value for x in d_pops]), byref(stats)), ctx)
     return stats.as_dict()
+
+
+def qsw_survival_time(ctx, op, d_rho0, t_end: float, q: int, sink: int, d_pops=None):
+    """Expected survival time (Simpson over the sink population); returns
+    (eta, series stats)."""
+    eta = c_double()
+    stats = qsw_series_stats()
+    _check(lib().qsw_survival_time(op, _ptr(d_rho0), float(t_end), int(q), int(sink), byref(eta),
+                                   _ptr(d_pops), byref(stats)), ctx)
+    return eta.value, stats.as_dict()
+
+
+def qsw_batch_survival_time(ctx, ops, d_rho0s, t_ends, qs, sinks):
+    """Expected survival times of many walks in one batched launch; returns
+    (list of eta, batch stats)."""
+    k = len(ops)
+    eta = (c_double * k)()
+    stats = qsw_batch_stats()
+    _check(lib().qsw_batch_survival_time(
+        ctx, k, (c_void_p * k)(*[o.value if isinstance(o, c_void_p) else o for o in ops]),
+        (c_void_p * k)(*[_ptr(x).value for x in d_rho0s]),
+        (c_double * k)(*[float(x) for x in t_ends]), (c_int32 * k)(*[int(x) for x in qs]),
+        (c_int32 * k)(*[int(x) for x in sinks]), eta, byref(stats)), ctx)
+    return list(eta), stats.as_dict()
 
 
 def qsw_server_create(device: int = 0, workers: int = 2, max_batch: int = 64,
