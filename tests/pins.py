@@ -30,9 +30,13 @@ def dense_jumps(G: np.ndarray, sources=(), sinks=()):
     return out
 
 
-def master_rhs(rho, H, jumps, omega):
-    """d rho / dt of the L-QSW master equation, evaluated directly."""
+def master_rhs(rho, H, jumps, omega, h_rot=None):
+    """d rho / dt of the master equation, evaluated directly: the L-QSW form, or
+    any list of Lindblad operators (G-QSW), plus +i omega [H_rot, rho] when a
+    rotating Hamiltonian is given (the NM-G-QSW form)."""
     out = -1j * (1 - omega) * (H @ rho - rho @ H)
+    if h_rot is not None:
+        out = out + 1j * omega * (h_rot @ rho - rho @ h_rot)
     for L, rate, scaled in jumps:
         w = rate * (omega if scaled else 1.0)
         LdL = L.conj().T @ L
@@ -40,7 +44,7 @@ def master_rhs(rho, H, jumps, omega):
     return out
 
 
-def brute_force_superoperator(H, jumps, omega):
+def brute_force_superoperator(H, jumps, omega, h_rot=None):
     """Column (m + N l) of L~ is vec(RHS(|m><l|)), column-major vec."""
     nt = H.shape[0]
     L = np.zeros((nt * nt, nt * nt), complex)
@@ -48,7 +52,7 @@ def brute_force_superoperator(H, jumps, omega):
         for m in range(nt):
             E = np.zeros((nt, nt), complex)
             E[m, l] = 1.0
-            L[:, m + nt * l] = master_rhs(E, H, jumps, omega).reshape(-1, order="F")
+            L[:, m + nt * l] = master_rhs(E, H, jumps, omega, h_rot).reshape(-1, order="F")
     return L
 
 
