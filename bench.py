@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--est-networks", type=int, default=4, help="est: dipole networks")
     ap.add_argument("--est-omegas", type=int, default=64, help="est: omega values per network")
     ap.add_argument("--est-precision", default="c128", choices=["c128", "c64"], help="est: precision")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45", "est"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45", "est", "gqsw"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -375,6 +375,76 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def run_gqsw_workload(args):
+    """G-QSW (Section 2.5.2: one global Lindblad operator L = G) on a directed
+    Erdos-Renyi digraph, N = 400, p = 0.025, w ~ U(0.5, 1.5), omega = 0.3,
+    uniform superposition, 50 steps of dt = 0.1, complex128.  One step = build
+    (Q = -i(1-omega)H - omega/2 G^T G on the host, norms on the device) + the
+    series with populations."""
+    import numpy as np
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(0, stream.cuda_stream)
+    g = W.erdos_renyi_digraph(400, 0.025, W.SEED_ER1000 + 1)
+    omega, steps, dt = 0.3, 50, 0.1
+    rho0 = torch.from_numpy(W.vec(W.uniform_superposition(400))).to(dev)
+    pops = torch.empty((steps + 1, 400), dtype=torch.float64, device=dev)
+
+    def step():
+        op = C.qsw_build_gqsw(ctx, g, None, omega)
+        st = C.qsw_expmv_series(ctx, op, rho0, 0.0, dt, steps, None, pops)
+        C.qsw_op_destroy(op)
+        return st
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = C.qsw_kernel_launches()
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (C.qsw_kernel_launches() - l0) / args.steps
+    C.qsw_destroy(ctx)
+    s0 = stats[-1]
+    peak = fp64_peak_tflops()
+    achieved = s0["algorithmic_flops"] / (s0["kernel_ms"] * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import time
+        from oracle import expmv, gqsw
+        t = time.perf_counter()
+        walk = gqsw.global_walk(g.dense())
+        L = gqsw.superoperator(walk, omega)
+        expmv.expmv_series(L, W.vec(W.uniform_superposition(400)), 0.0, dt, 2)
+        sec = time.perf_counter() - t
+        cpu = {"value": 2.0 / sec, "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"Kronecker G-QSW superoperator + Algorithm 5.2 over the first 2 output "
+                         f"times, {sec:.1f} s"}
+    line = {"metric": "G-QSW walk time-steps/s (global Lindblad operator, whole path)",
+            "value": steps * 1000.0 / ms, "unit": "time-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic (seeded Erdos-Renyi digraph)",
+            "config": {"workload": "gqsw", "graph": "Erdos-Renyi digraph N=400 p=0.025",
+                       "omega": omega, "series_steps": steps, "dt": dt},
+            "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "series_kernel (global walk)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak},
+            "series": {"kernel_ms": s0["kernel_ms"], "matvecs": s0["matvecs"],
+                       "m_star": s0["m_star"], "s": s0["s"]},
+            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
+    print(json.dumps(line))
+
+
 def run_est_workload(args):
     """Expected-survival-time sweep (Section 4.1.4): `--est-networks` dipole
     networks of 10 points uniform in the unit ball (V = -d^-3, source and sink of
@@ -676,6 +746,9 @@ def main():
         return
     if args.workload == "est":
         run_est_workload(args)
+        return
+    if args.workload == "gqsw":
+        run_gqsw_workload(args)
         return
     run_ours(args)
 

@@ -122,6 +122,18 @@ typedef struct {
                                 term of a Hermitian matrix is Hermitian) */
 } qsw_series_stats;
 
+/* A complex sparse matrix in CSR (host arrays): row i holds columns
+ * col[rowptr[i] .. rowptr[i+1]-1], strictly increasing, values re + i im
+ * (im may be NULL for a real matrix). */
+typedef struct {
+  int32_t n;
+  int32_t nnz;
+  const int32_t* rowptr;
+  const int32_t* col;
+  const double* re;
+  const double* im;
+} qsw_zcsr;
+
 /* ---------------------------------------------------------------- context */
 
 /* Create a context on CUDA device `device`, issuing all work on `cuda_stream`
@@ -292,6 +304,35 @@ qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,
                             const double* dt, const int32_t* steps, double* const* d_pops,
                             qsw_batch_stats* stats);
+
+/* ------------------------------------------ global-interaction walks */
+
+/* A global-interaction walk (G-QSW, Section 2.5.2, Eq. L_global; the
+ * non-moralising NM-G-QSW of Eq. nm_gqsw): on n_vertices vertices plus the
+ * ports,
+ *   d rho/dt = -i(1-omega)[H, rho] + omega sum_k (L_k rho L_k^dag - 1/2 {L_k^dag L_k, rho})
+ *              + i omega [H_rot, rho] + (source / sink terms as for the L-QSW),
+ * with H (Hermitian, required), n_L <= 8 Lindblad operators L_k (any complex
+ * n_vertices x n_vertices matrices) and an optional Hermitian H_rot (NULL:
+ * none).  The operator is matrix-free (no CSR form: qsw_op_info reports
+ * nnz = 0 and qsw_op_export_csr is refused); qsw_expmv_series,
+ * qsw_survival_time, qsw_apply, qsw_populations, qsw_initial_state and
+ * qsw_set_omega accept it; the batched and no-allocation entry points do not.
+ * ||L~||_1 is exact for one L_k without diagonal entries, estimated
+ * otherwise.  flags: 0 or QSW_BUILD_DEFER_NORMS.
+ * Errors: INVALID_ARG, OMEGA_RANGE, NOT_HERMITIAN, TOO_LARGE, OOM, CUDA. */
+qsw_status qsw_build_global(qsw_ctx* ctx, int32_t n_vertices, const qsw_zcsr* H,
+                            const qsw_zcsr* Ls, int32_t n_L, const qsw_zcsr* H_rot, double omega,
+                            const qsw_port* sources, int32_t n_sources, const qsw_port* sinks,
+                            int32_t n_sinks, int32_t precision, int32_t flags, qsw_op** op);
+
+/* The G-QSW of digraph G (Section 2.5.2): one Lindblad operator
+ * L_global = sum_ij G_ij |v_i><v_j| (G itself, row = destination) and H as
+ * passed, or trans(1, G^u) (the Laplacian of the undirected companion) when H
+ * is NULL.  Errors as qsw_build_superoperator. */
+qsw_status qsw_build_gqsw(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, double omega,
+                          const qsw_port* sources, int32_t n_sources, const qsw_port* sinks,
+                          int32_t n_sinks, int32_t precision, qsw_op** op);
 
 /* ------------------------------------------- expected survival time */
 

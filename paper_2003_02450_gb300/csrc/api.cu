@@ -90,7 +90,103 @@ void check_ports(const qsw_port* p, int count, int N, const char* name) {
   }
 }
 
+// A complex host CSR (qsw_zcsr) as a ZMat, with the structural checks of
+// check_csr; `hermitian` also requires A = A^dag.
+qsw::ZMat zmat_of(const qsw_zcsr* m, int n, const char* name, bool hermitian) {
+  const std::string nm(name);
+  QSW_CHECK_ARG(m != nullptr, QSW_ERR_INVALID_ARG, nm + " is NULL");
+  QSW_CHECK_ARG(m->n == n, QSW_ERR_INVALID_ARG, nm + " must be N x N");
+  QSW_CHECK_ARG(m->nnz >= 0 && m->rowptr != nullptr, QSW_ERR_INVALID_ARG, nm + ": bad nnz/rowptr");
+  QSW_CHECK_ARG(m->nnz == 0 || (m->col && m->re), QSW_ERR_INVALID_ARG, nm + ".col/.re is NULL");
+  QSW_CHECK_ARG(m->rowptr[0] == 0 && m->rowptr[n] == m->nnz, QSW_ERR_INVALID_ARG,
+                nm + ".rowptr must start at 0 and end at nnz");
+  qsw::ZMat z;
+  z.n = n;
+  z.rowptr.assign(m->rowptr, m->rowptr + n + 1);
+  for (int i = 0; i < n; ++i) {
+    QSW_CHECK_ARG(m->rowptr[i] <= m->rowptr[i + 1], QSW_ERR_INVALID_ARG,
+                  nm + ".rowptr is not non-decreasing");
+    for (int e = m->rowptr[i]; e < m->rowptr[i + 1]; ++e) {
+      const int c = m->col[e];
+      QSW_CHECK_ARG(c >= 0 && c < n, QSW_ERR_INVALID_ARG, nm + ": column index out of range");
+      QSW_CHECK_ARG(e == m->rowptr[i] || m->col[e - 1] < c, QSW_ERR_INVALID_ARG,
+                    nm + ": columns must be strictly increasing within a row");
+      const double im = m->im ? m->im[e] : 0.0;
+      QSW_CHECK_ARG(isfinite(m->re[e]) && isfinite(im), QSW_ERR_INVALID_ARG, nm + ": non-finite value");
+      z.col.push_back(c);
+      z.val.push_back(std::complex<double>(m->re[e], im));
+    }
+  }
+  if (hermitian)
+    for (int i = 0; i < n; ++i)
+      for (int e = z.rowptr[i]; e < z.rowptr[i + 1]; ++e) {
+        const int j = z.col[e];
+        const int* b = z.col.data() + z.rowptr[j];
+        const int* f = z.col.data() + z.rowptr[j + 1];
+        const int* q = std::lower_bound(b, f, i);
+        QSW_CHECK_ARG(q != f && *q == i && z.val[q - z.col.data()] == std::conj(z.val[e]),
+                      QSW_ERR_NOT_HERMITIAN, nm + " must be Hermitian");
+      }
+  return z;
+}
+
+// trans(1, G^u): the Laplacian of the undirected companion, G^u = max(G, G^T)
+qsw::ZMat laplacian_undirected(const qsw_csr* G) {
+  const int n = G->n;
+  std::vector<std::vector<std::pair<int, double>>> rows(n);
+  for (int i = 0; i < n; ++i)
+    for (int e = G->rowptr[i]; e < G->rowptr[i + 1]; ++e) {
+      rows[i].push_back({G->col[e], G->w[e]});
+      rows[G->col[e]].push_back({i, G->w[e]});
+    }
+  qsw::ZMat L;
+  L.n = n;
+  L.rowptr.assign(n + 1, 0);
+  for (int i = 0; i < n; ++i) {
+    auto& r = rows[i];
+    std::sort(r.begin(), r.end());
+    std::vector<std::pair<int, double>> u;   // max over the two directions
+    for (auto& e : r) {
+      if (!u.empty() && u.back().first == e.first) u.back().second = std::max(u.back().second, e.second);
+      else u.push_back(e);
+    }
+    double deg = 0.0;
+    for (auto& e : u) deg += e.second;
+    bool placed = false;
+    for (auto& e : u) {
+      if (!placed && e.first > i) {
+        L.col.push_back(i);
+        L.val.push_back(deg);
+        placed = true;
+      }
+      L.col.push_back(e.first);
+      L.val.push_back(-e.second);
+    }
+    if (!placed) {
+      L.col.push_back(i);
+      L.val.push_back(deg);
+    }
+    L.rowptr[i + 1] = (int)L.col.size();
+  }
+  return L;
+}
+
+qsw::ZMat zmat_of_real(const qsw_csr* G) {
+  qsw::ZMat z;
+  z.n = G->n;
+  z.rowptr.assign(G->rowptr, G->rowptr + G->n + 1);
+  z.col.assign(G->col, G->col + G->nnz);
+  for (int e = 0; e < G->nnz; ++e) z.val.push_back(G->w[e]);
+  return z;
+}
+
 void rebuild(Op& op, bool defer_norms) {
+  if (op.gq.active) {   // global-interaction walk: matrix-free only
+    qsw::build_global(op);
+    op.norms_ready = !defer_norms;
+    if (!defer_norms) qsw::compute_norms(op, nullptr, nullptr);
+    return;
+  }
   qsw::build_jumps(op);
   qsw::prep_matfree(op);
   op.L = qsw::Csr{};
@@ -227,6 +323,80 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
   });
 }
 
+qsw_status qsw_build_global(qsw_ctx* ctx, int32_t n_vertices, const qsw_zcsr* H,
+                            const qsw_zcsr* Ls, int32_t n_L, const qsw_zcsr* H_rot, double omega,
+                            const qsw_port* sources, int32_t n_sources, const qsw_port* sinks,
+                            int32_t n_sinks, int32_t precision, int32_t flags, qsw_op** out) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr && out != nullptr, QSW_ERR_INVALID_ARG, "ctx/out is NULL");
+    *out = nullptr;
+    QSW_CHECK_ARG(n_vertices >= 1, QSW_ERR_INVALID_ARG, "n_vertices must be >= 1");
+    QSW_CHECK_ARG(n_L >= 0 && n_L <= qsw::kMaxGlobalOps && (n_L == 0 || Ls), QSW_ERR_INVALID_ARG,
+                  "n_L must be 0.." + std::to_string(qsw::kMaxGlobalOps));
+    QSW_CHECK_ARG(isfinite(omega) && omega >= 0.0 && omega <= 1.0, QSW_ERR_OMEGA_RANGE,
+                  "omega must lie in [0, 1]");
+    QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
+                  "unknown precision");
+    QSW_CHECK_ARG((flags & ~QSW_BUILD_DEFER_NORMS) == 0, QSW_ERR_INVALID_ARG, "unknown flags");
+    check_ports(sources, n_sources, n_vertices, "sources");
+    check_ports(sinks, n_sinks, n_vertices, "sinks");
+    const long long Nt = (long long)n_vertices + n_sources + n_sinks;
+    QSW_CHECK_ARG(Nt * Nt < (1LL << 31) - 1, QSW_ERR_TOO_LARGE, "N~^2 does not fit 32-bit indices");
+    std::unique_ptr<Op> op(new Op());
+    op->gq.H = zmat_of(H, n_vertices, "H", true);
+    for (int k = 0; k < n_L; ++k)
+      op->gq.Ls.push_back(zmat_of(&Ls[k], n_vertices, "L", false));
+    if (H_rot) op->gq.Hrot = zmat_of(H_rot, n_vertices, "H_rot", true);
+    set_device(ctx);
+    op->gq.active = true;
+    op->ctx = ctx;
+    op->precision = precision;
+    op->opkind = QSW_OPERATOR_MATRIX_FREE;
+    op->omega = omega;
+    op->N = n_vertices;
+    op->Nt = (int)Nt;
+    op->n = Nt * Nt;
+    for (int k = 0; k < n_sources; ++k) {
+      op->src_v.push_back(sources[k].vertex);
+      op->src_r.push_back(sources[k].rate);
+    }
+    for (int k = 0; k < n_sinks; ++k) {
+      op->snk_v.push_back(sinks[k].vertex);
+      op->snk_r.push_back(sinks[k].rate);
+    }
+    rebuild(*op, (flags & QSW_BUILD_DEFER_NORMS) != 0);
+    *out = reinterpret_cast<qsw_op*>(op.release());
+  });
+}
+
+qsw_status qsw_build_gqsw(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, double omega,
+                          const qsw_port* sources, int32_t n_sources, const qsw_port* sinks,
+                          int32_t n_sinks, int32_t precision, qsw_op** out) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr && out != nullptr, QSW_ERR_INVALID_ARG, "ctx/out is NULL");
+    check_csr(G, "G", false);
+    for (int e = 0; e < G->nnz; ++e)
+      QSW_CHECK_ARG(G->w[e] > 0.0, QSW_ERR_NOT_SIMPLE, "G: arc weights must be > 0");
+    qsw::ZMat h;
+    if (H) {
+      check_csr(H, "H", true);
+      QSW_CHECK_ARG(H->n == G->n, QSW_ERR_INVALID_ARG, "H must be N x N");
+      h = zmat_of_real(H);
+    } else {
+      h = laplacian_undirected(G);
+    }
+    const qsw::ZMat l = zmat_of_real(G);
+    std::vector<double> hre, hi, lre;
+    for (auto& v : h.val) hre.push_back(v.real());
+    for (auto& v : l.val) lre.push_back(v.real());
+    const qsw_zcsr hz{h.n, (int32_t)h.col.size(), h.rowptr.data(), h.col.data(), hre.data(), nullptr};
+    const qsw_zcsr lz{l.n, (int32_t)l.col.size(), l.rowptr.data(), l.col.data(), lre.data(), nullptr};
+    const qsw_status st = qsw_build_global(ctx, G->n, &hz, &lz, 1, nullptr, omega, sources,
+                                           n_sources, sinks, n_sinks, precision, 0, out);
+    if (st != QSW_OK) throw Error{st, ctx->last_error};
+  });
+}
+
 qsw_status qsw_set_omega(qsw_op* h, double omega) {
   Op* op = reinterpret_cast<Op*>(h);
   return guarded(op ? op->ctx : nullptr, [&] {
@@ -260,6 +430,8 @@ qsw_status qsw_op_export_csr(const qsw_op* h, int32_t* d_rowptr, int32_t* d_col,
     QSW_CHECK_ARG(op != nullptr, QSW_ERR_INVALID_ARG, "op is NULL");
     set_device(op->ctx);
     cudaStream_t st = op->ctx->stream;
+    QSW_CHECK_ARG(!op->gq.active, QSW_ERR_INVALID_ARG,
+                  "global-interaction walks are matrix-free only (no CSR form)");
     qsw::Csr tmp;
     const qsw::Csr* L = &op->L;
     if (op->opkind != QSW_OPERATOR_CSR) {   // assemble on demand, FP64
@@ -366,6 +538,8 @@ qsw_status qsw_expmv_series_noalloc(qsw_op* h, const double* d_rho0, double t0, 
     QSW_CHECK_ARG(op->norms_ready, QSW_ERR_INVALID_ARG,
                   "operator built with QSW_BUILD_DEFER_NORMS: its norms need workspace; "
                   "run qsw_expmv_series once first");
+    QSW_CHECK_ARG(!op->gq.active, QSW_ERR_INVALID_ARG,
+                  "global-interaction walks need a pass-A workspace; use qsw_expmv_series");
     set_device(op->ctx);
     qsw::run_series_noalloc(*op, d_rho0, t0, dt, steps, d_out, d_pops, stats);
   });

@@ -889,8 +889,8 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   QSW_CUDA_TRY(cudaMemsetAsync(hb.p, 0, hb.bytes, st));
   for (int w = 0; w < count; ++w) {
     const Op& op = *ops[w];
-    QSW_CHECK_ARG(op.opkind == QSW_OPERATOR_MATRIX_FREE, QSW_ERR_INVALID_ARG,
-                  "batched series needs matrix-free operators");
+    QSW_CHECK_ARG(op.opkind == QSW_OPERATOR_MATRIX_FREE && !op.gq.active, QSW_ERR_INVALID_ARG,
+                  "batched series needs matrix-free L-QSW operators");
     QSW_LAUNCH herm_check_many<<<grid_for(op.n * n0, 256, 1024), 256, 0, st>>>(
         op.Nt, op.n, n0, reinterpret_cast<const double2*>(d_rho0[w]),
         hb.as<unsigned long long>() + 2 * w);

@@ -294,6 +294,9 @@ struct Estimator {
         const Csr& M = adjoint ? *AH : *A;
         QSW_LAUNCH spmm_kernel<<<grid_for((long long)n * 8, 256, 152 * 16), 256, 0, st>>>(
             n, t, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
+      } else if (op->gq.active) {
+        gq_apply64(*op, adjoint, t, reinterpret_cast<const double*>(src),
+                   reinterpret_cast<double*>(dst), 1.0);
       } else {
         mf_apply64(*op, adjoint, t, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), 1.0);
@@ -406,11 +409,15 @@ struct Estimator {
 void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   cudaStream_t st = op.ctx->stream;
   const int n = (int)op.n;
-  // exact ||L||_1
+  // exact ||L||_1 (global walks: closed form when it applies, else estimated below)
+  bool one_estimated = false;
+  double one = 0.0;
   DevBuf bits;
   bits.alloc(sizeof(unsigned long long));
   QSW_CUDA_TRY(cudaMemsetAsync(bits.p, 0, sizeof(unsigned long long), st));
-  if (LH) {
+  if (op.gq.active) {
+    one_estimated = !global_exact_norm(op, &one);
+  } else if (LH) {
     QSW_LAUNCH rowabs_max_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, st>>>(
         n, LH->rowptr.as<int>(), LH->val.as<double2>(), bits.as<unsigned long long>());
   } else {
@@ -418,13 +425,13 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
         op.Nt, op.mf.habs.as<double>(), op.mf.ad64.as<double>(), op.mf.hw64.as<double>(),
         op.g.dtot.as<double>(), bits.as<unsigned long long>());
   }
-  QSW_CUDA_TRY(cudaGetLastError());
-  unsigned long long b = 0;
-  QSW_CUDA_TRY(cudaMemcpyAsync(&b, bits.p, sizeof(b), cudaMemcpyDeviceToHost, st));
-  QSW_CUDA_TRY(cudaStreamSynchronize(st));
-  double one;
-  memcpy(&one, &b, sizeof(one));
-  op.norms[0] = one;
+  if (!op.gq.active) {
+    QSW_CUDA_TRY(cudaGetLastError());
+    unsigned long long b = 0;
+    QSW_CUDA_TRY(cudaMemcpyAsync(&b, bits.p, sizeof(b), cudaMemcpyDeviceToHost, st));
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(&one, &b, sizeof(one));
+  }
 
   Estimator E;
   E.st = st;
@@ -441,7 +448,13 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.pv.alloc(sizeof(double) * kRedGrid);
   E.pi.alloc(sizeof(int) * kRedGrid);
   E.out.alloc(sizeof(double) * 4);
-  if (one != 0.0) E.make_chain(kNormPowers);
+  if (one_estimated) {   // several sandwich operators (or diagonal entries): estimate p = 1 too
+    E.make_chain(kNormPowers);
+    one = E.estimate(1);
+  } else if (one != 0.0) {
+    E.make_chain(kNormPowers);
+  }
+  op.norms[0] = one;
   for (int p = 2; p <= kNormPowers; ++p) op.norms[p - 1] = one == 0.0 ? 0.0 : E.estimate(p);
 
   // d_p = ||L^p||_1^(1/p), taken on the device; the host keeps a copy for sizing.

@@ -1,6 +1,8 @@
 // Context and operator objects behind the opaque handles of qsw.h.
 #pragma once
 
+#include <complex>
+
 #include "qsw_internal.h"
 
 struct qsw_ctx {
@@ -50,6 +52,34 @@ struct MfData {
   DevBuf pwin;             // [ceil(Nt / 64)] 1 where that order pairs the rows
 };
 
+// A complex matrix in CSR on the host (columns increasing within a row).
+struct ZMat {
+  int n = 0;
+  std::vector<int> rowptr, col;
+  std::vector<std::complex<double>> val;
+};
+
+// Global-interaction walk (G-QSW / NM-G-QSW): host operators and the device
+// form of gqsw.cuh (rebuilt for every omega).
+struct GlobalData {
+  bool active = false;
+  ZMat H, Hrot;               // N x N; Hrot.n == 0: no rotating Hamiltonian
+  std::vector<ZMat> Ls;       // N x N Lindblad operators
+  int nl = 0;                 // operators in the sandwich (0 at omega = 0)
+  bool exact_norm = false;    // ||L~||_1 in closed form (one operator, no diagonal)
+  long long nnz_q = 0, nnz_l = 0;
+  DevBuf q_rowptr, q_col, q_val64, q_val32;       // Q
+  DevBuf qh_rowptr, qh_col, qh_val64, qh_val32;   // Q^dag
+  DevBuf l_rowptr[kMaxGlobalOps], l_col[kMaxGlobalOps], l_val64[kMaxGlobalOps],
+      l_val32[kMaxGlobalOps];                      // L'_k = sqrt(omega) L_k
+  DevBuf lh_rowptr[kMaxGlobalOps], lh_col[kMaxGlobalOps], lh_val64[kMaxGlobalOps],
+      lh_val32[kMaxGlobalOps];                     // L'_k^dag
+  DevBuf j_rowptr, j_col, j_val64, j_val32;       // port jumps (rows = target)
+  DevBuf jt_rowptr, jt_col, jt_val64, jt_val32;   // transposed
+  DevBuf cq, qdiag, cl, jout;                     // exact 1-norm ingredients
+  DevBuf west;                                    // pass-A scratch of the estimator
+};
+
 struct Op {
   qsw_ctx* ctx = nullptr;
   int precision = QSW_C128;
@@ -69,6 +99,7 @@ struct Op {
 
   GraphDev g;
   MfData mf;
+  GlobalData gq;   // global-interaction walks only
   Csr L;           // the superoperator in CSR (assembled for QSW_OPERATOR_CSR or on export)
   double norms[kNormPowers] = {0};   // ||L||_1, est ||L^p||_1
   double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
@@ -78,6 +109,7 @@ struct Op {
 
   // series workspace
   DevBuf kbuf, ring, jobs, ctrl, scratch;
+  DevBuf scratch_w;   // global walks: pass-A products
 };
 
 // graph.cu
@@ -87,6 +119,12 @@ void build_jumps(Op& op);           // J, J^T, dtot for op.omega
 void assemble(Op& op, bool adjoint, Csr& out);   // L (adjoint = false) or L^H, FP64 values
 void to_fp32(Op& op, Csr& m);                    // replace FP64 values by FP32
 void prep_matfree(Op& op);         // MfData for op.omega
+// gqsw.cu
+void build_global(Op& op);                        // device form for op.omega
+template <class R> struct GqOp;
+template <class R> GqOp<R> make_gq(const Op& op, bool adjoint);
+void gq_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
+bool global_exact_norm(const Op& op, double* one);
 // norms.cu
 void compute_norms(Op& op, const Csr* L, const Csr* LH);   // null: matrix-free
 // series.cu

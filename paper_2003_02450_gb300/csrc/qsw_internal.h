@@ -17,6 +17,7 @@ constexpr int kPMax = 8;      // p_max (largest p with p(p-1) <= m_max + 1)
 constexpr int kEll = 2;       // columns of the 1-norm estimator
 constexpr int kNormPowers = 9;  // ||L^p||_1, p = 1..9 (paper Section 4 footnote)
 constexpr int kMaxPorts = 4096;
+constexpr int kMaxGlobalOps = 8;   // Lindblad operators of a global-interaction walk
 
 // Number of kernels this library has launched in this process (all devices).
 extern std::atomic<long long> g_launches;

@@ -32,6 +32,7 @@
 #include <mutex>
 #include <string>
 
+#include "gqsw.cuh"
 #include "matfree.cuh"
 #include "op.h"
 #include "params.cuh"
@@ -50,7 +51,7 @@ constexpr int kRpt = 2;                 // rows per thread in one matrix-free pa
 constexpr unsigned kSpinLimit = 1u << 24;  // bounded barrier wait (~seconds)
 
 enum : int { kErrNone = 0, kErrBarrier = 1, kErrPlan = 2 };
-enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2 };
+enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2, kOpGlobal = 3, kOpGlobalHerm = 4 };
 static_assert(kItemRows == 32 * kRpt, "a work item is one row per lane per kRpt");
 
 struct Ctrl {
@@ -61,7 +62,7 @@ struct Ctrl {
   unsigned long long matvecs;
   unsigned long long fupdates;   // sum over terms of the outputs updated
   unsigned int work[3];          // matrix-free column counters, one per term slot
-  unsigned int pad;
+  unsigned int work2[3];         // global walks: pass-A counters
   unsigned long long gmax[3][1 + kDMax];
 };
 
@@ -72,6 +73,9 @@ struct SeriesArgs {
   const void* val;
   MfOp<double> mf64;     // matrix-free operator (one of the two is used)
   MfOp<float> mf32;
+  GqOp<double> gq64;     // global-interaction walk (one of the two is used)
+  GqOp<float> gq32;
+  void* wbuf;            // its pass-A products, nl x n
   void* k0;
   void* k1;
   const double2* rho0;
@@ -93,6 +97,7 @@ template <> struct Cplx<double2> {
     return make_double2(a, __longlong_as_double(__double_as_longlong(b) ^ (1LL << 63)));
   }
   __device__ static const MfOp<double>& mf(const SeriesArgs& a) { return a.mf64; }
+  __device__ static const GqOp<double>& gq(const SeriesArgs& a) { return a.gq64; }
 };
 template <> struct Cplx<float2> {
   using R = float;
@@ -101,6 +106,7 @@ template <> struct Cplx<float2> {
     return make_float2(a, __int_as_float(__float_as_int(b) ^ (int)0x80000000));
   }
   __device__ static const MfOp<float>& mf(const SeriesArgs& a) { return a.mf32; }
+  __device__ static const GqOp<float>& gq(const SeriesArgs& a) { return a.gq32; }
 };
 
 __device__ __forceinline__ double2* slot_ptr(const SeriesArgs& a, int idx) {
@@ -257,7 +263,7 @@ series_kernel(SeriesArgs a) {
     unsigned long long zmax = 0;
     for (long long r = gthread; r < a.n; r += nthreads) {
       double2 z;
-      if (OPK == kOpMatfreeHerm) {
+      if (OPK == kOpMatfreeHerm || OPK == kOpGlobalHerm) {
         // only upper triangles are maintained: read (i, j), i > j, as conj(Z(j, i))
         const int i = (int)(r % a.nt), j = (int)(r / a.nt);
         if (i > j) {
@@ -285,7 +291,10 @@ series_kernel(SeriesArgs a) {
     if (blockIdx.x == 0) {
       const unsigned nx = (term + 1) % 3;
       for (int q = tid; q <= J.d; q += kBlock) ctrl->gmax[nx][q] = 0ULL;
-      if (tid == 0) ctrl->work[nx] = 0u;
+      if (tid == 0) {
+        ctrl->work[nx] = 0u;
+        ctrl->work2[nx] = 0u;
+      }
     }
     if (!grid_barrier(ctrl)) return;
     const double normz = sqrt(from_bits(__ldcg(&ctrl->gmax[slot3][0])));
@@ -323,7 +332,55 @@ series_kernel(SeriesArgs a) {
         ep.fmax[u] = 0;
       }
 
-      if (OPK != kOpCsr) {
+      if (OPK == kOpGlobal || OPK == kOpGlobalHerm) {
+        // ---- global walk: pass A (W_k = K L'_k^dag, every element), a grid
+        // barrier, then pass B (the term, upper triangle for Hermitian input)
+        constexpr bool kHerm = OPK == kOpGlobalHerm;
+        const GqOp<R>& op = Cplx<VT>::gq(a);
+        VT* w = static_cast<VT*>(a.wbuf);
+        const int nt = a.nt;
+        if (op.nl || kHerm) {
+          const long long nall = mf_item_count(nt, false);
+          for (;;) {
+            unsigned int k = 0;
+            if (lane == 0) k = atomicAdd(&ctrl->work2[slot3], 1u);
+            k = __shfl_sync(0xffffffffu, k, 0);
+            if ((long long)k >= nall) break;
+            int j, a0;
+            mf_item(k, nt, false, j, a0);
+            int arow[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int r = a0 + lane + 32 * u;
+              arow[u] = r < nt ? r : -1;
+            }
+            gq_pass_a<R, VT>(op, kcur, w, j, arow);
+            if (kHerm) gq_pass_a_r<R, VT>(op, kcur, w, j, arow);
+          }
+          if (!grid_barrier(ctrl)) return;
+        }
+        const long long nitems = mf_item_count(nt, kHerm);
+        for (;;) {
+          unsigned int k = 0;
+          if (lane == 0) k = atomicAdd(&ctrl->work[slot3], 1u);
+          k = __shfl_sync(0xffffffffu, k, 0);
+          if ((long long)k >= nitems) break;
+          int j, i0;
+          mf_item(k, nt, kHerm, j, i0);
+#pragma unroll
+          for (int u = 0; u < kRpt; ++u) {
+            const int i = i0 + lane + 32 * u;
+            if (i >= nt || (kHerm && i > j)) continue;
+            R yx, yy;
+            if (kHerm) gq_element_herm<R, VT>(op, kcur, w, i, j, yx, yy);
+            else gq_element<R, VT>(op, kcur, w, i, j, yx, yy);
+            yx *= rscale;
+            yy *= rscale;
+            ep.consume(i + (long long)nt * j, yx, yy);
+            if (kHerm && i != j) knext[j + (long long)nt * i] = Cplx<VT>::conj_of(yx, yy);
+          }
+        }
+      } else if (OPK != kOpCsr) {
         // ---- matrix-free sweep: warps take 64-row chunks of columns from a
         // counter (no block-level synchronisation inside the pass)
         constexpr bool kHerm = OPK == kOpMatfreeHerm;
@@ -421,6 +478,7 @@ series_kernel(SeriesArgs a) {
         for (int q = tid; q <= J.d; q += kBlock) ctrl->gmax[nx][q] = 0ULL;
         if (tid == 0) {
           ctrl->work[nx] = 0u;
+          ctrl->work2[nx] = 0u;
           int act = 0;
           for (int k = 0; k < J.d; ++k) act += s_active[k];
           atomicAdd(&ctrl->matvecs, 1ULL);
@@ -451,7 +509,7 @@ series_kernel(SeriesArgs a) {
     }
 
     // ---- Hermitian form: complete the caller's outputs from their upper triangles
-    if (OPK == kOpMatfreeHerm && a.mirror && J.final_outputs) {
+    if ((OPK == kOpMatfreeHerm || OPK == kOpGlobalHerm) && a.mirror && J.final_outputs) {
       const long long tot = (long long)J.d * a.n;
       for (long long q = gthread; q < tot; q += nthreads) {
         const int k = (int)(q / a.n);
@@ -609,8 +667,9 @@ cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* gr
       &per_sm, series_kernel<VT, OPK, TPR>, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
-  const long long want = OPK != kOpCsr ? (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps
-                                       : ((long long)a.n * TPR + kBlock - 1) / kBlock;
+  const long long want =
+      OPK == kOpCsr ? ((long long)a.n * TPR + kBlock - 1) / kBlock
+                    : (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps;
   const long long maxg = (long long)per_sm * sms;
   const int grid = (int)std::max<long long>(1, std::min(want, maxg));
   *grid_out = grid;
@@ -624,6 +683,9 @@ cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* gr
 template <class VT>
 cudaError_t launch_series_op(const Op& op, int tpr, bool herm, const SeriesArgs& a, int sms,
                              cudaStream_t st, int* g) {
+  if (op.gq.active)
+    return herm ? launch_series<VT, kOpGlobalHerm, 1>(a, sms, st, g)
+                : launch_series<VT, kOpGlobal, 1>(a, sms, st, g);
   if (op.opkind == QSW_OPERATOR_MATRIX_FREE)
     return herm ? launch_series<VT, kOpMatfreeHerm, 1>(a, sms, st, g)
                 : launch_series<VT, kOpMatfree, 1>(a, sms, st, g);
@@ -690,6 +752,8 @@ void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y
 
 double op_bytes(const Op& op) {
   const bool f32 = op.precision == QSW_C64_BULK;
+  if (op.gq.active)   // Q and L' rows: column index + complex value
+    return (double)(op.gq.nnz_q + op.gq.nnz_l) * (4.0 + (f32 ? sizeof(float2) : sizeof(double2)));
   if (op.opkind == QSW_OPERATOR_CSR)
     return (double)op.L.nnz * ((f32 ? sizeof(float2) : sizeof(double2)) + 4) +
            (double)(op.n + 1) * 4;
@@ -747,6 +811,11 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
     a.rowptr = op.L.rowptr.as<int>();
     a.col = op.L.col.as<int>();
     a.val = op.L.val.p;
+  } else if (op.gq.active) {
+    a.gq64 = make_gq<double>(op, false);
+    a.gq32 = make_gq<float>(op, false);
+    op.scratch_w.alloc(vbytes * (size_t)(op.gq.nl + 1) * (size_t)op.n);   // W_k, then R
+    a.wbuf = op.scratch_w.p;
   } else {
     a.mf64 = make_mf<double>(op, false);
     a.mf32 = make_mf<float>(op, false);
@@ -806,12 +875,28 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
     // off-diagonal terms and N~(N~+1)/2 elements
     const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
     const double elems = frac * (double)op.n;
-    const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
-    const double flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems +
-                                    4.0 * op.g.n_jumps + 5.0 * elems;
+    double flops_per_matvec;
+    if (op.gq.active) {
+      // pass A: 8 flops per (element, entry of row j of L'); pass B: 8 per
+      // entry of rows i and j of Q and of row i of L' (complex products)
+      const double nt = op.Nt;
+      flops_per_matvec = 8.0 * nt * (double)op.gq.nnz_l +
+                         frac * 8.0 * nt * (2.0 * (double)op.gq.nnz_q + (double)op.gq.nnz_l) +
+                         5.0 * elems;
+    } else {
+      const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
+      flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems + 4.0 * op.g.n_jumps + 5.0 * elems;
+    }
     stats->algorithmic_flops = stats->matvecs * flops_per_matvec + 7.0 * elems * h.fupdates;
+    if (op.gq.active) {
+      // pass A writes and pass B reads the W products
+      stats->bytes_per_matvec += 2.0 * vbytes * (double)op.gq.nl * (double)op.n;
+      stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
+                                 32.0 * (double)op.n * (double)h.fupdates + init_bytes;
+    }
     if (herm) {
-      stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes;
+      stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes +
+                                (op.gq.active ? 2.0 * vbytes * (double)op.gq.nl * (double)op.n : 0.0);
       stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
                                  32.0 * elems * (double)h.fupdates + init_bytes;
     }
@@ -974,6 +1059,10 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
 }
 
 void apply(const Op& op, const double* d_x, double* d_y) {
+  if (op.gq.active) {
+    gq_apply64(op, false, 1, d_x, d_y, 1.0);
+    return;
+  }
   cudaStream_t st = op.ctx->stream;
   const int n = (int)op.n;
   if (op.opkind == QSW_OPERATOR_MATRIX_FREE) {

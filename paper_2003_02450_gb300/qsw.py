@@ -60,6 +60,11 @@ class qsw_series_stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class qsw_zcsr(ctypes.Structure):
+    _fields_ = [("n", c_int32), ("nnz", c_int32), ("rowptr", POINTER(c_int32)),
+                ("col", POINTER(c_int32)), ("re", POINTER(c_double)), ("im", POINTER(c_double))]
+
+
 class qsw_batch_stats(ctypes.Structure):
     _fields_ = [("walks", c_int32), ("clusters", c_int32), ("norms_ms", c_double),
                 ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64),
@@ -110,6 +115,11 @@ _SIGNATURES = {
     "qsw_expmv_series_host": ([c_void_p, c_void_p, c_double, c_double, c_int32, c_void_p,
                                c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
+    "qsw_build_global": ([c_void_p, c_int32, POINTER(qsw_zcsr), POINTER(qsw_zcsr), c_int32,
+                          POINTER(qsw_zcsr), c_double, POINTER(qsw_port), c_int32,
+                          POINTER(qsw_port), c_int32, c_int32, c_int32, POINTER(c_void_p)], c_int32),
+    "qsw_build_gqsw": ([c_void_p, POINTER(qsw_csr), POINTER(qsw_csr), c_double, POINTER(qsw_port),
+                        c_int32, POINTER(qsw_port), c_int32, c_int32, POINTER(c_void_p)], c_int32),
     "qsw_survival_time": ([c_void_p, c_void_p, c_double, c_int32, c_int32, POINTER(c_double),
                            c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_batch_survival_time": ([c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p),
@@ -179,6 +189,24 @@ class _Csr:
                          self.w.ctypes.data_as(POINTER(c_double)))
 
 
+class _ZCsr:
+    """A complex CSR view of any scipy-convertible matrix (arrays kept alive)."""
+
+    def __init__(self, m):
+        import scipy.sparse as sp
+        m = sp.csr_matrix(m, dtype=np.complex128)
+        m.sort_indices()
+        self.rowptr = np.ascontiguousarray(m.indptr, dtype=np.int32)
+        self.col = np.ascontiguousarray(m.indices, dtype=np.int32)
+        self.re = np.ascontiguousarray(m.data.real, dtype=np.float64)
+        self.im = np.ascontiguousarray(m.data.imag, dtype=np.float64)
+        self.c = qsw_zcsr(int(m.shape[0]), int(self.col.size),
+                          self.rowptr.ctypes.data_as(POINTER(c_int32)),
+                          self.col.ctypes.data_as(POINTER(c_int32)),
+                          self.re.ctypes.data_as(POINTER(c_double)),
+                          self.im.ctypes.data_as(POINTER(c_double)))
+
+
 def _as_csr(g):
     if g is None:
         return None
@@ -228,6 +256,38 @@ def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sink
     op = c_void_p()
     st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
                                        src, nsrc, snk, nsnk, int(prec), int(kind), byref(op))
+    _check(st, ctx)
+    return op
+
+
+def qsw_build_global(ctx, n_vertices: int, H, Ls=(), H_rot=None, omega: float = 0.5, sources=(),
+                     sinks=(), precision="c128", defer_norms: bool = False):
+    """Global-interaction walk (G-QSW / NM-G-QSW) from explicit operators:
+    H (Hermitian), Lindblad operators Ls, optional rotating Hamiltonian H_rot."""
+    h = _ZCsr(H)
+    ls = [_ZCsr(L) for L in Ls]
+    arr = (qsw_zcsr * max(1, len(ls)))(*[z.c for z in ls])
+    rot = _ZCsr(H_rot) if H_rot is not None else None
+    src, nsrc = _ports(sources)
+    snk, nsnk = _ports(sinks)
+    op = c_void_p()
+    st = lib().qsw_build_global(ctx, int(n_vertices), byref(h.c), arr, len(ls),
+                                byref(rot.c) if rot else None, float(omega), src, nsrc, snk, nsnk,
+                                int(PRECISIONS.get(precision, precision)),
+                                QSW_BUILD_DEFER_NORMS if defer_norms else 0, byref(op))
+    _check(st, ctx)
+    return op
+
+
+def qsw_build_gqsw(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(), precision="c128"):
+    """G-QSW of digraph G: L = [G], H as passed or the Laplacian of G^u."""
+    g = _as_csr(G)
+    h = _as_csr(H)
+    src, nsrc = _ports(sources)
+    snk, nsnk = _ports(sinks)
+    op = c_void_p()
+    st = lib().qsw_build_gqsw(ctx, byref(g.c), byref(h.c) if h else None, float(omega), src, nsrc,
+                              snk, nsnk, int(PRECISIONS.get(precision, precision)), byref(op))
     _check(st, ctx)
     return op
 
