@@ -53,7 +53,7 @@ def parse_args():
     ap.add_argument("--est-networks", type=int, default=4, help="est: dipole networks")
     ap.add_argument("--est-omegas", type=int, default=64, help="est: omega values per network")
     ap.add_argument("--est-precision", default="c128", choices=["c128", "c64"], help="est: precision")
-    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45", "est", "gqsw"],
+    ap.add_argument("--workload", default=WORKLOAD, choices=[WORKLOAD, "batch256", "serve2000", "grid45", "est", "gqsw", "nmgqsw"],
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
@@ -445,6 +445,82 @@ def run_gqsw_workload(args):
     print(json.dumps(line))
 
 
+def run_nm_workload(args):
+    """NM-G-QSW (Section 2.5.2, Eq. nm_gqsw) of a directed Erdos-Renyi digraph,
+    N = 60, p = 0.06, w ~ U(0.5, 1.5), demoralised to N^D = sum_v deg_{G^u}(v)
+    copies; omega = 0.3, uniform vertex populations, 20 steps of dt = 0.1,
+    complex128.  One step = demoralise + build + series + population map."""
+    import numpy as np
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    from paper_2003_02450_gb300 import workloads as W
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    ctx = C.qsw_create(0, stream.cuda_stream)
+    g = W.erdos_renyi_digraph(60, 0.06, W.SEED_ER1000 + 2)
+    omega, steps, dt = 0.3, 20, 0.1
+    probe = C.qsw_build_nm_gqsw(ctx, g, omega)
+    nd = C.qsw_op_info(ctx, probe)["n_tilde"]
+    C.qsw_op_destroy(probe)
+    state = torch.empty(nd * nd, dtype=torch.complex128, device=dev)
+    pe = torch.empty((steps + 1, nd), dtype=torch.float64, device=dev)
+    p = torch.empty((steps + 1, 60), dtype=torch.float64, device=dev)
+    pops0 = np.full(60, 1.0 / 60)
+
+    def step():
+        op = C.qsw_build_nm_gqsw(ctx, g, omega)
+        C.qsw_nm_initial_state(ctx, op, pops0, state)
+        st = C.qsw_expmv_series(ctx, op, state, 0.0, dt, steps, None, pe)
+        C.qsw_nm_populations(ctx, op, pe, steps + 1, p)
+        C.qsw_op_destroy(op)
+        return st
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = C.qsw_kernel_launches()
+    e0.record(stream)
+    stats = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (C.qsw_kernel_launches() - l0) / args.steps
+    C.qsw_destroy(ctx)
+    s0 = stats[-1]
+    peak = fp64_peak_tflops()
+    achieved = s0["algorithmic_flops"] / (s0["kernel_ms"] * 1e-3) / 1e12
+    cpu = None
+    if not args.no_cpu_baseline:
+        import time
+        from oracle import expmv, gqsw, nm
+        t = time.perf_counter()
+        walk, vs = nm.nm_walk(g.dense())
+        L = gqsw.superoperator(walk, omega)
+        expmv.expmv_series(L, W.vec(nm.initial_state(pops0, vs)), 0.0, dt, 1)
+        sec = time.perf_counter() - t
+        cpu = {"value": 1.0 / sec, "unit": "time-steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"demoralisation + Kronecker superoperator + Algorithm 5.2 over the first "
+                         f"output time, {sec:.1f} s"}
+    line = {"metric": "NM-G-QSW walk time-steps/s (demoralised digraph, whole path)",
+            "value": steps * 1000.0 / ms, "unit": "time-steps/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+            "data": "synthetic (seeded Erdos-Renyi digraph)",
+            "config": {"workload": "nmgqsw", "graph": "Erdos-Renyi digraph N=60 p=0.06",
+                       "expanded_vertices": nd, "omega": omega, "series_steps": steps, "dt": dt},
+            "roofline": {"bound": "alu", "pipe": "fp64", "kernel": "series_kernel (global walk)",
+                         "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak},
+            "series": {"kernel_ms": s0["kernel_ms"], "matvecs": s0["matvecs"],
+                       "m_star": s0["m_star"], "s": s0["s"]},
+            "gpu_launches": launches, "clocks": clocks, "cpu_baseline": cpu}
+    print(json.dumps(line))
+
+
 def run_est_workload(args):
     """Expected-survival-time sweep (Section 4.1.4): `--est-networks` dipole
     networks of 10 points uniform in the unit ball (V = -d^-3, source and sink of
@@ -749,6 +825,9 @@ def main():
         return
     if args.workload == "gqsw":
         run_gqsw_workload(args)
+        return
+    if args.workload == "nmgqsw":
+        run_nm_workload(args)
         return
     run_ours(args)
 

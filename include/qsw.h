@@ -334,6 +334,33 @@ qsw_status qsw_build_gqsw(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, doub
                           const qsw_port* sources, int32_t n_sources, const qsw_port* sinks,
                           int32_t n_sinks, int32_t precision, qsw_op** op);
 
+/* The non-moralising G-QSW of digraph G (Section 2.5.2 "Graph
+ * Demoralisation", Eq. nm_gqsw): vertex v becomes d_v = max(1, deg_{G^u}(v))
+ * copies; H^D = trans(1, G^{uD}) with G^{uD} weights w / sqrt(d_v d_u); one
+ * Lindblad operator L^D that sends each copy of u, for an arc u -> v, to the
+ * Fourier column F_{d_v}[., c_v(u)] (F_d[j, c] = exp(2 pi i j c / d), c_v(u)
+ * the position of u among v's sorted G^u neighbours) with amplitude
+ * w / sqrt(d_v d_u); the rotating Hamiltonian <v^{k+1}|H_rot|v^k> = i.  The
+ * operator lives on the N^D = sum_v d_v copies (qsw_op_info: N~ = N^D); use
+ * qsw_nm_initial_state and qsw_nm_populations for vertex populations.
+ * Errors as qsw_build_superoperator. */
+qsw_status qsw_build_nm_gqsw(qsw_ctx* ctx, const qsw_csr* G, double omega, int32_t precision,
+                             qsw_op** op);
+
+/* offsets[v] .. offsets[v+1]-1 index vertex v's copies (host array of N+1).
+ * Errors: INVALID_ARG (not an NM-G-QSW operator). */
+qsw_status qsw_nm_vsets(const qsw_op* op, int32_t* offsets);
+
+/* Eq. nm_rho_map for `count` population vectors: d_pops[c N + v] = sum over
+ * v's copies k of d_pops_expanded[c N^D + k] (device arrays).  Synchronises. */
+qsw_status qsw_nm_populations(const qsw_op* op, const double* d_pops_expanded, int32_t count,
+                              double* d_pops);
+
+/* rho^D(0) with vertex populations h_pops (host, N values summing to 1)
+ * spread uniformly over each vertex's copies (diagonal), into d_state
+ * (N^D x N^D complex128, device).  Synchronises. */
+qsw_status qsw_nm_initial_state(const qsw_op* op, const double* h_pops, double* d_state);
+
 /* ------------------------------------------- expected survival time */
 
 /* Expected survival time of a walk with a sink (Section 4.1.4, transport

@@ -397,6 +397,83 @@ qsw_status qsw_build_gqsw(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr* H, doub
   });
 }
 
+qsw_status qsw_build_nm_gqsw(qsw_ctx* ctx, const qsw_csr* G, double omega, int32_t precision,
+                             qsw_op** out) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr && out != nullptr, QSW_ERR_INVALID_ARG, "ctx/out is NULL");
+    check_csr(G, "G", false);
+    for (int e = 0; e < G->nnz; ++e)
+      QSW_CHECK_ARG(G->w[e] > 0.0, QSW_ERR_NOT_SIMPLE, "G: arc weights must be > 0");
+    std::vector<int> off;
+    qsw::ZMat hd, ld, hr;
+    qsw::nm_construct(G->n, G->rowptr, G->col, G->w, off, hd, ld, hr);
+    auto view = [](const qsw::ZMat& m, std::vector<double>& re, std::vector<double>& im) {
+      for (auto& v : m.val) {
+        re.push_back(v.real());
+        im.push_back(v.imag());
+      }
+      return qsw_zcsr{m.n, (int32_t)m.col.size(), m.rowptr.data(), m.col.data(), re.data(),
+                      im.data()};
+    };
+    std::vector<double> a, b, c, d, e, f;
+    const qsw_zcsr hz = view(hd, a, b), lz = view(ld, c, d), rz = view(hr, e, f);
+    const qsw_status st = qsw_build_global(ctx, hd.n, &hz, &lz, 1, &rz, omega, nullptr, 0, nullptr,
+                                           0, precision, 0, out);
+    if (st != QSW_OK) throw Error{st, ctx->last_error};
+    Op* op = reinterpret_cast<Op*>(*out);
+    op->gq.vset_off = off;
+    op->gq.vset_dev.alloc(sizeof(int) * off.size());
+    QSW_CUDA_TRY(cudaMemcpyAsync(op->gq.vset_dev.p, off.data(), sizeof(int) * off.size(),
+                                 cudaMemcpyHostToDevice, ctx->stream));
+    QSW_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
+  });
+}
+
+qsw_status qsw_nm_vsets(const qsw_op* h, int32_t* offsets) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op && offsets, QSW_ERR_INVALID_ARG, "op/offsets is NULL");
+    QSW_CHECK_ARG(!op->gq.vset_off.empty(), QSW_ERR_INVALID_ARG, "not an NM-G-QSW operator");
+    memcpy(offsets, op->gq.vset_off.data(), sizeof(int32_t) * op->gq.vset_off.size());
+  });
+}
+
+qsw_status qsw_nm_populations(const qsw_op* h, const double* d_pops_expanded, int32_t count,
+                              double* d_pops) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op && d_pops_expanded && d_pops && count >= 0, QSW_ERR_INVALID_ARG,
+                  "bad arguments to qsw_nm_populations");
+    QSW_CHECK_ARG(!op->gq.vset_off.empty(), QSW_ERR_INVALID_ARG, "not an NM-G-QSW operator");
+    set_device(op->ctx);
+    if (count) qsw::nm_populations(*op, d_pops_expanded, count, d_pops);
+    QSW_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));
+  });
+}
+
+qsw_status qsw_nm_initial_state(const qsw_op* h, const double* h_pops, double* d_state) {
+  const Op* op = reinterpret_cast<const Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op && h_pops && d_state, QSW_ERR_INVALID_ARG, "op/pops/d_state is NULL");
+    QSW_CHECK_ARG(!op->gq.vset_off.empty(), QSW_ERR_INVALID_ARG, "not an NM-G-QSW operator");
+    const int N = (int)op->gq.vset_off.size() - 1;
+    double sum = 0.0;
+    for (int v = 0; v < N; ++v) {
+      QSW_CHECK_ARG(isfinite(h_pops[v]) && h_pops[v] >= 0.0, QSW_ERR_INVALID_ARG,
+                    "populations must be finite and >= 0");
+      sum += h_pops[v];
+    }
+    QSW_CHECK_ARG(fabs(sum - 1.0) <= 1e-12, QSW_ERR_INVALID_ARG, "populations must sum to 1");
+    set_device(op->ctx);
+    qsw::DevBuf p;
+    p.alloc(sizeof(double) * N);
+    QSW_CUDA_TRY(cudaMemcpyAsync(p.p, h_pops, sizeof(double) * N, cudaMemcpyHostToDevice,
+                                 op->ctx->stream));
+    qsw::nm_initial_state(*op, p.as<double>(), d_state);
+    QSW_CUDA_TRY(cudaStreamSynchronize(op->ctx->stream));
+  });
+}
+
 qsw_status qsw_set_omega(qsw_op* h, double omega) {
   Op* op = reinterpret_cast<Op*>(h);
   return guarded(op ? op->ctx : nullptr, [&] {

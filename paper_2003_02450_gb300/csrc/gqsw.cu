@@ -77,15 +77,21 @@ ZMat axpby(cd alpha, const ZMat& a, cd beta, const ZMat& b) {
   return c;
 }
 
-// a^dag a
+// a^dag a.  An entry whose computed magnitude is within its own rounding
+// error (16 eps times the sum of its terms' magnitudes) is dropped: such sums
+// cancel exactly in exact arithmetic (the demoralised operator's Fourier
+// columns of different in-neighbours are orthogonal) and would only fill Q
+// with rounding residue.
 ZMat gram(const ZMat& a) {
   const ZMat ah = adjoint(a);
   ZMat g;
   g.n = a.n;
   g.rowptr.assign(a.n + 1, 0);
   std::vector<cd> acc(a.n);
+  std::vector<double> mag(a.n);
   std::vector<char> hit(a.n, 0);
   std::vector<int> touched;
+  const double eps = 2.220446049250313e-16;
   for (int i = 0; i < a.n; ++i) {
     touched.clear();
     for (int e = ah.rowptr[i]; e < ah.rowptr[i + 1]; ++e) {   // (a^dag)_{i r} = conj(a_{r i})
@@ -95,15 +101,19 @@ ZMat gram(const ZMat& a) {
         if (!hit[m]) {
           hit[m] = 1;
           acc[m] = 0.0;
+          mag[m] = 0.0;
           touched.push_back(m);
         }
         acc[m] += ah.val[e] * a.val[f];
+        mag[m] += std::abs(ah.val[e]) * std::abs(a.val[f]);
       }
     }
     std::sort(touched.begin(), touched.end());
     for (int m : touched) {
-      g.col.push_back(m);
-      g.val.push_back(acc[m]);
+      if (std::abs(acc[m]) > 16.0 * eps * mag[m]) {
+        g.col.push_back(m);
+        g.val.push_back(acc[m]);
+      }
       hit[m] = 0;
     }
     g.rowptr[i + 1] = (int)g.col.size();
@@ -378,6 +388,171 @@ bool global_exact_norm(const Op& op, double* one) {
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
   memcpy(one, &b, sizeof(double));
   return true;
+}
+
+// ------------------------------------------------------- NM-G-QSW (demoralised)
+// Section 2.5.2 "Graph Demoralisation", in these readings: vertex v becomes
+// d_v = max(1, deg_{G^u}(v)) copies; G^{uD} joins every copy of v to every copy
+// of each G^u neighbour u with weight w^u / sqrt(d_v d_u); H^D = trans(1, G^{uD});
+// an arc u -> v of weight w sends each copy of u to the Fourier column
+// F_{d_v}[., c_v(u)] (c_v(u) = u's position among v's sorted G^u neighbours,
+// F_d[j, c] = exp(2 pi i j c / d)) with amplitude w / sqrt(d_v d_u); H_rot has
+// <v^{k+1}|H_rot|v^k> = i within each subspace (one pair when d = 2).
+void nm_construct(int N, const int* rowptr, const int* col, const double* w, std::vector<int>& off,
+                  ZMat& Hd, ZMat& Ld, ZMat& Hrot) {
+  // G^u neighbours with weights max(G_vu, G_uv), sorted
+  std::vector<std::vector<std::pair<int, double>>> nb(N);
+  for (int v = 0; v < N; ++v)
+    for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+      nb[v].push_back({col[e], w[e]});
+      nb[col[e]].push_back({v, w[e]});
+    }
+  for (auto& r : nb) {
+    std::sort(r.begin(), r.end());
+    std::vector<std::pair<int, double>> u;
+    for (auto& e : r) {
+      if (!u.empty() && u.back().first == e.first) u.back().second = std::max(u.back().second, e.second);
+      else u.push_back(e);
+    }
+    r.swap(u);
+  }
+  off.assign(N + 1, 0);
+  for (int v = 0; v < N; ++v) off[v + 1] = off[v] + std::max<int>(1, (int)nb[v].size());
+  const int ND = off[N];
+  auto dim = [&](int v) { return off[v + 1] - off[v]; };
+  // H^D
+  Hd = ZMat{};
+  Hd.n = ND;
+  Hd.rowptr.assign(ND + 1, 0);
+  for (int v = 0; v < N; ++v) {
+    const int dv = dim(v);
+    double deg = 0.0;
+    for (auto& e : nb[v]) deg += dim(e.first) * e.second / sqrt((double)dv * dim(e.first));
+    for (int j = 0; j < dv; ++j) {
+      const int row = off[v] + j;
+      bool placed = false;
+      for (auto& e : nb[v]) {
+        const int u = e.first, du = dim(u);
+        if (!placed && u > v) {
+          Hd.col.push_back(row);
+          Hd.val.push_back(deg);
+          placed = true;
+        }
+        const double h = -e.second / sqrt((double)dv * du);
+        for (int l = 0; l < du; ++l) {
+          Hd.col.push_back(off[u] + l);
+          Hd.val.push_back(h);
+        }
+      }
+      if (!placed) {
+        Hd.col.push_back(row);
+        Hd.val.push_back(deg);
+      }
+      Hd.rowptr[row + 1] = (int)Hd.col.size();
+    }
+  }
+  // L^D: rows are copies of the arc's target v, columns copies of its source u
+  Ld = ZMat{};
+  Ld.n = ND;
+  Ld.rowptr.assign(ND + 1, 0);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int v = 0; v < N; ++v) {
+    const int dv = dim(v);
+    for (int j = 0; j < dv; ++j) {
+      const int row = off[v] + j;
+      for (int e = rowptr[v]; e < rowptr[v + 1]; ++e) {   // arcs u -> v, u increasing
+        const int u = col[e], du = dim(u);
+        int c = 0;
+        while (nb[v][c].first != u) ++c;
+        const std::complex<double> f = std::polar(1.0, two_pi * (double)((long long)j * c % dv) / dv);
+        const std::complex<double> a = f * (w[e] / sqrt((double)dv * du));
+        for (int l = 0; l < du; ++l) {
+          Ld.col.push_back(off[u] + l);
+          Ld.val.push_back(a);
+        }
+      }
+      Ld.rowptr[row + 1] = (int)Ld.col.size();
+    }
+  }
+  // H_rot
+  std::vector<std::vector<std::pair<int, std::complex<double>>>> rr(ND);
+  for (int v = 0; v < N; ++v) {
+    const int d = dim(v), b = off[v];
+    const std::complex<double> I(0.0, 1.0);
+    if (d == 2) {
+      rr[b + 1].push_back({b, I});
+      rr[b].push_back({b + 1, -I});
+    } else if (d >= 3) {
+      for (int k = 0; k < d; ++k) {
+        const int k1 = (k + 1) % d;
+        rr[b + k1].push_back({b + k, I});
+        rr[b + k].push_back({b + k1, -I});
+      }
+    }
+  }
+  Hrot = ZMat{};
+  Hrot.n = ND;
+  Hrot.rowptr.assign(ND + 1, 0);
+  for (int i = 0; i < ND; ++i) {
+    std::sort(rr[i].begin(), rr[i].end(),
+              [](const std::pair<int, std::complex<double>>& x,
+                 const std::pair<int, std::complex<double>>& y) { return x.first < y.first; });
+    for (auto& e : rr[i]) {
+      Hrot.col.push_back(e.first);
+      Hrot.val.push_back(e.second);
+    }
+    Hrot.rowptr[i + 1] = (int)Hrot.col.size();
+  }
+}
+
+namespace {
+
+__global__ void nm_pops_kernel(int count, int N, int ND, const int* __restrict__ off,
+                               const double* __restrict__ pe, double* __restrict__ p) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < (long long)count * N;
+       q += (long long)gridDim.x * blockDim.x) {
+    const long long c = q / N;
+    const int v = (int)(q % N);
+    double s = 0.0;
+    for (int k = off[v]; k < off[v + 1]; ++k) s += pe[c * ND + k];
+    p[q] = s;
+  }
+}
+
+__global__ void nm_init_kernel(int N, int ND, const int* __restrict__ off,
+                               const double* __restrict__ p, double2* __restrict__ state) {
+  const long long n = (long long)ND * ND;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(r % ND), j = (int)(r / ND);
+    double v = 0.0;
+    if (i == j) {
+      int lo = 0, hi = N - 1;   // vertex whose copies hold i
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= i) lo = mid;
+        else hi = mid - 1;
+      }
+      v = p[lo] / (double)(off[lo + 1] - off[lo]);
+    }
+    state[r] = make_double2(v, 0.0);
+  }
+}
+
+}  // namespace
+
+void nm_populations(const Op& op, const double* d_pe, int count, double* d_p) {
+  const int N = (int)op.gq.vset_off.size() - 1;
+  QSW_LAUNCH nm_pops_kernel<<<grid_for((long long)count * N, 256, 4096), 256, 0, op.ctx->stream>>>(
+      count, N, op.Nt, op.gq.vset_dev.as<int>(), d_pe, d_p);
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
+void nm_initial_state(const Op& op, const double* d_p, double* d_state) {
+  const int N = (int)op.gq.vset_off.size() - 1;
+  QSW_LAUNCH nm_init_kernel<<<grid_for(op.n, 256, 4096), 256, 0, op.ctx->stream>>>(
+      N, op.Nt, op.gq.vset_dev.as<int>(), d_p, reinterpret_cast<double2*>(d_state));
+  QSW_CUDA_TRY(cudaGetLastError());
 }
 
 }  // namespace qsw

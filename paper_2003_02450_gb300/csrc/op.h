@@ -78,6 +78,8 @@ struct GlobalData {
   DevBuf jt_rowptr, jt_col, jt_val64, jt_val32;   // transposed
   DevBuf cq, qdiag, cl, jout;                     // exact 1-norm ingredients
   DevBuf west;                                    // pass-A scratch of the estimator
+  std::vector<int> vset_off;  // NM-G-QSW: copies of vertex v are vset_off[v] .. vset_off[v+1]-1
+  DevBuf vset_dev;
 };
 
 struct Op {
@@ -125,6 +127,10 @@ template <class R> struct GqOp;
 template <class R> GqOp<R> make_gq(const Op& op, bool adjoint);
 void gq_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
 bool global_exact_norm(const Op& op, double* one);
+void nm_construct(int N, const int* rowptr, const int* col, const double* w, std::vector<int>& off,
+                  ZMat& Hd, ZMat& Ld, ZMat& Hrot);
+void nm_populations(const Op& op, const double* d_pe, int count, double* d_p);
+void nm_initial_state(const Op& op, const double* d_p, double* d_state);
 // norms.cu
 void compute_norms(Op& op, const Csr* L, const Csr* LH);   // null: matrix-free
 // series.cu

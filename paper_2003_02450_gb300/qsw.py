@@ -120,6 +120,11 @@ _SIGNATURES = {
                           POINTER(qsw_port), c_int32, c_int32, c_int32, POINTER(c_void_p)], c_int32),
     "qsw_build_gqsw": ([c_void_p, POINTER(qsw_csr), POINTER(qsw_csr), c_double, POINTER(qsw_port),
                         c_int32, POINTER(qsw_port), c_int32, c_int32, POINTER(c_void_p)], c_int32),
+    "qsw_build_nm_gqsw": ([c_void_p, POINTER(qsw_csr), c_double, c_int32, POINTER(c_void_p)],
+                          c_int32),
+    "qsw_nm_vsets": ([c_void_p, POINTER(c_int32)], c_int32),
+    "qsw_nm_populations": ([c_void_p, c_void_p, c_int32, c_void_p], c_int32),
+    "qsw_nm_initial_state": ([c_void_p, POINTER(c_double), c_void_p], c_int32),
     "qsw_survival_time": ([c_void_p, c_void_p, c_double, c_int32, c_int32, POINTER(c_double),
                            c_void_p, POINTER(qsw_series_stats)], c_int32),
     "qsw_batch_survival_time": ([c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p),
@@ -290,6 +295,30 @@ def qsw_build_gqsw(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(), pre
                               snk, nsnk, int(PRECISIONS.get(precision, precision)), byref(op))
     _check(st, ctx)
     return op
+
+
+def qsw_build_nm_gqsw(ctx, G, omega: float = 0.5, precision="c128"):
+    """Non-moralising G-QSW of digraph G on its demoralised vertex copies."""
+    g = _as_csr(G)
+    op = c_void_p()
+    _check(lib().qsw_build_nm_gqsw(ctx, byref(g.c), float(omega),
+                                   int(PRECISIONS.get(precision, precision)), byref(op)), ctx)
+    return op
+
+
+def qsw_nm_vsets(ctx, op, n_vertices: int) -> np.ndarray:
+    off = np.zeros(n_vertices + 1, dtype=np.int32)
+    _check(lib().qsw_nm_vsets(op, off.ctypes.data_as(POINTER(c_int32))), ctx)
+    return off
+
+
+def qsw_nm_populations(ctx, op, d_pops_expanded, count: int, d_pops) -> None:
+    _check(lib().qsw_nm_populations(op, _ptr(d_pops_expanded), int(count), _ptr(d_pops)), ctx)
+
+
+def qsw_nm_initial_state(ctx, op, pops, d_state) -> None:
+    p = np.ascontiguousarray(pops, dtype=np.float64)
+    _check(lib().qsw_nm_initial_state(op, p.ctypes.data_as(POINTER(c_double)), _ptr(d_state)), ctx)
 
 
 def qsw_set_omega(ctx, op, omega: float) -> None:
