@@ -46,7 +46,9 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
 constexpr int kDMax = 128;              // outputs per Taylor block
-constexpr int kKReg = 4;                // outputs whose running max lives in registers
+constexpr int kKReg = 2;                // outputs whose running max lives in registers (the
+                                        // rest use shared memory): 2 keeps the kernel at 64
+                                        // registers, 4 blocks (32 warps) per SM
 constexpr int kRpt = 2;                 // rows per thread in one matrix-free pass
 constexpr unsigned kSpinLimit = 1u << 24;  // bounded barrier wait (~seconds)
 
@@ -233,7 +235,7 @@ template <class VT> struct Epilogue {
 };
 
 template <class VT, int OPK, int TPR>
-__global__ void __launch_bounds__(kBlock, 3)
+__global__ void __launch_bounds__(kBlock, 4)
 series_kernel(SeriesArgs a) {
   using R = typename Cplx<VT>::R;
   __shared__ unsigned long long s_red[kWarps][1 + kKReg];
