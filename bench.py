@@ -189,6 +189,31 @@ def measured_peak_gbs():
 DFMA_PER_CYCLE = 304
 
 
+KERNEL_SOURCES = ["paper_2003_02450_gb300/csrc/series.cu", "paper_2003_02450_gb300/csrc/matfree.cuh",
+                  "paper_2003_02450_gb300/csrc/params.cuh", "paper_2003_02450_gb300/csrc/gqsw.cuh"]
+
+
+def series_traffic():
+    """DRAM bytes of one full-size series launch from the committed ncu summary,
+    or None when the kernel sources changed since that capture."""
+    import hashlib
+    import re
+    h = hashlib.sha256()
+    try:
+        for f in KERNEL_SOURCES:
+            with open(os.path.join(ROOT, f), "rb") as fh:
+                h.update(fh.read())
+        with open(os.path.join(ROOT, "profiles", "series_kernel_er1000.md")) as fh:
+            text = fh.read()
+    except OSError:
+        return None
+    m_hash = re.search(r"kernel sources sha256: ([0-9a-f]{64})", text)
+    m_bytes = re.search(r"dram bytes per full launch: ([0-9]+)", text)
+    if not m_hash or not m_bytes or m_hash.group(1) != h.hexdigest():
+        return None
+    return int(m_bytes.group(1))
+
+
 def fp64_peak_tflops():
     mhz = 2070.0
     try:
@@ -329,7 +354,7 @@ def run_ours(args):
                          "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
                          "frac": achieved_tf / fp64_peak,
                          "peak_source": "304 DFMA/cycle x 2 flop x max SM clock (ncu peak_sustained)",
-                         "traffic": None, "algorithmic_flops_per_launch": alg_flops,
+                         "traffic": series_traffic() if args.operator == "matfree" else None, "traffic_unit": "bytes per launch (ncu dram read + write)", "algorithmic_flops_per_launch": alg_flops,
                          "kernel_ms": kern_ms,
                          "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak, "peak_source": peak_kind,
