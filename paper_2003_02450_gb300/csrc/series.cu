@@ -196,7 +196,9 @@ template <> struct NormKey<float2> {
 // Per-thread epilogue state of one Taylor term.
 template <class VT> struct Epilogue {
   using R = typename Cplx<VT>::R;
-  const SeriesArgs* a;
+  double2* slots;       // the outputs (caller's array or ring) and their layout
+  int ring;
+  long long n;
   VT* knext;
   int out0, d;
   double coef[kKReg];
@@ -207,6 +209,10 @@ template <class VT> struct Epilogue {
   const int* s_active;
   unsigned long long* s_fmax_extra;   // outputs k >= kKReg (shared, block-level keys)
 
+  __device__ __forceinline__ double2* slot(int idx) const {
+    return slots + (long long)(ring ? idx % ring : idx) * n;
+  }
+
   __device__ void consume(long long r, R yx, R yy) {
     knext[r] = Cplx<VT>::make(yx, yy);
     kmax = umax64(kmax, NormKey<VT>::y(yx, yy));
@@ -214,7 +220,7 @@ template <class VT> struct Epilogue {
 #pragma unroll
     for (int u = 0; u < kKReg; ++u) {
       if (own[u]) {
-        double2* F = slot_ptr(*a, out0 + u) + r;
+        double2* F = slot(out0 + u) + r;
         double2 f = __ldcg(F);
         f.x = fma(coef[u], dx, f.x);
         f.y = fma(coef[u], dy, f.y);
@@ -224,7 +230,7 @@ template <class VT> struct Epilogue {
     }
     for (int k = kKReg; k < d; ++k) {
       if (!s_active[k]) continue;
-      double2* F = slot_ptr(*a, out0 + k) + r;
+      double2* F = slot(out0 + k) + r;
       double2 f = __ldcg(F);
       f.x = fma(s_coef[k], dx, f.x);
       f.y = fma(s_coef[k], dy, f.y);
@@ -319,7 +325,9 @@ series_kernel(SeriesArgs a) {
       }
       __syncthreads();
       Epilogue<VT> ep;
-      ep.a = &a;
+      ep.slots = a.slots;
+      ep.ring = a.ring;
+      ep.n = a.n;
       ep.knext = knext;
       ep.out0 = J.out_index0;
       ep.d = J.d;
