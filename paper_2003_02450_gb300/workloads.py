@@ -250,7 +250,7 @@ SEED_EST = 7440
 
 
 def est_dipole(count: int = 4, n: int = 10, omegas: int = 64, seed: int = SEED_EST,
-               t_end: float = 40.0, q: int = 400):
+               t_end: float = 300.0, q: int = 600):
     """Expected-survival-time sweep (Section 4.1.4): `count` dipole networks of
     n points, each with a source (rate 0.5) feeding vertex 0 and a sink (rate
     0.5) draining vertex n - 1, for omega = k / omegas, k = 1..omegas.  The

@@ -121,3 +121,27 @@ def test_survival_time_rejects_bad_grids(ctx):
     eta, _ = C.qsw_survival_time(ctx.handle, op, _rho0(4), 10.0, 4, 5)   # still usable
     assert np.isfinite(eta)
     C.qsw_op_destroy(op)
+
+
+def test_full_sweep_sampled_walks(ctx):
+    """The bench's sweep (4 networks x 64 omega, t_end 300, q 600) in one
+    batched call; two of its walks recomputed by the oracle."""
+    from paper_2003_02450_gb300 import qsw as C
+    walks = W.est_dipole()
+    ops = [C.qsw_build_superoperator(ctx.handle, w["graph"], w["H"], w["omega"], w["sources"],
+                                     w["sinks"], defer_norms=True) for w in walks]
+    rhos = [_rho0(w["graph"].n) for w in walks]
+    etas, stats = C.qsw_batch_survival_time(ctx.handle, ops, rhos, [w["t_end"] for w in walks],
+                                            [w["q"] for w in walks], [w["sink"] for w in walks])
+    assert stats["walks"] == 256 and len(etas) == 256
+    for k in (5, 64 * 3 + 40):
+        w = walks[k]
+        walk = graph.lqsw_walk(graph.adjacency(w["graph"]), H=w["H"], sources=w["sources"],
+                               sinks=w["sinks"])
+        L = superop.superoperator(walk, w["omega"])
+        ref, pops = est.survival_time(L, walk.n_tilde, W.vec(w["rho0"]), w["t_end"], w["q"],
+                                      w["sink"])
+        assert 1.0 - pops[-1, w["sink"]] < 1e-5          # t_end covers the decay
+        assert abs(etas[k] - ref) <= w["t_end"] * 1e-10
+    for op in ops:
+        C.qsw_op_destroy(op)

@@ -179,3 +179,20 @@ def test_gqsw_set_omega_and_limits(ctx):
     with pytest.raises(C.QswError):
         C.qsw_expmv_series_noalloc(ctx.handle, op, _dev(x), 0.0, 0.5, 2, None, pops)
     C.qsw_op_destroy(op)
+
+
+def test_bench_config_first_outputs_full_size(ctx):
+    """The G-QSW bench walk (ER N = 400, p = 0.025, omega = 0.3, uniform
+    superposition): the first two outputs of dt = 0.1 against the oracle."""
+    import torch
+    from paper_2003_02450_gb300 import qsw as C
+    g = W.erdos_renyi_digraph(400, 0.025, W.SEED_ER1000 + 1)
+    op = C.qsw_build_gqsw(ctx.handle, g, None, 0.3)
+    walk = gqsw.global_walk(g.dense())
+    L = gqsw.superoperator(walk, 0.3)
+    x0 = W.vec(W.uniform_superposition(400))
+    ref = expmv.expmv_series(L, x0, 0.0, 0.1, 2)
+    out = torch.empty((3, 400 * 400), dtype=torch.complex128, device="cuda:0")
+    C.qsw_expmv_series(ctx.handle, op, _dev(x0), 0.0, 0.1, 2, out, None)
+    assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-10
+    C.qsw_op_destroy(op)

@@ -111,3 +111,18 @@ def test_series_matches_oracle(ctx, name, seed):
     pref = nm.populations(superop.populations(ref, walk.n_tilde), vs)
     assert np.max(np.abs(p - pref)) <= 1e-10
     assert np.allclose(p.sum(axis=1), 1.0, atol=1e-12)
+
+
+def test_bench_config_first_output_full_size(ctx):
+    """The NM-G-QSW bench walk (ER N = 60, p = 0.06, 424 copies, omega = 0.3,
+    uniform vertex populations): the populations at t = 0.1 against the oracle."""
+    g = W.erdos_renyi_digraph(60, 0.06, W.SEED_ER1000 + 2)
+    G = g.dense()
+    pops0 = np.full(60, 1.0 / 60)
+    _, p = _run(ctx, G, 0.3, pops0, 0.0, 0.1, 1)
+    walk, vs = nm.nm_walk(G)
+    assert walk.n_tilde == 424
+    L = gqsw.superoperator(walk, 0.3)
+    ref = expmv.expmv_series(L, W.vec(nm.initial_state(pops0, vs)), 0.0, 0.1, 1)
+    pref = nm.populations(superop.populations(ref, walk.n_tilde), vs)
+    assert np.max(np.abs(p - pref)) <= 1e-10
