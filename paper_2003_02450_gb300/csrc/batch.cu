@@ -28,6 +28,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <numeric>
 #include <type_traits>
 
@@ -873,6 +874,22 @@ __global__ void herm_check_many(int Nt, long long n, int cols, const double2* __
   }
 }
 
+// The small-walk kernel's dynamic shared-memory limit is a property of the
+// function on a device, shared by every thread and stream: it is raised once
+// per device to the largest size any batch uses (kSmallTotalBytes), never
+// lowered, so that concurrent batches (the server's workers) cannot undercut
+// each other's launches.
+void allow_small_smem(int device) {
+  static std::mutex mu;
+  static bool done[64] = {};
+  QSW_CHECK_ARG(device >= 0 && device < 64, QSW_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[device]) return;
+  QSW_CUDA_TRY(cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)kSmallTotalBytes));
+  done[device] = true;
+}
+
 }  // namespace
 
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
@@ -1026,8 +1043,7 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   cudaEvent_t fork = nullptr, join = nullptr;
   if (!small.empty()) {
     const int dyn = (int)small_bytes;
-    QSW_CUDA_TRY(cudaFuncSetAttribute(batch_small_kernel,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, dyn));
+    allow_small_smem(ctx->device);
     int per_sm = 0;
     QSW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_small_kernel, kBT, dyn));
     const int grid = std::max(1, std::min((int)small.size(), std::max(1, per_sm) * ctx->num_sms));

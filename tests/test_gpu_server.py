@@ -105,3 +105,34 @@ def test_server_isolates_bad_requests_and_oversized_ones():
         g, omega, rho0, t0, steps, prec = r.meta
         tol = 1e-10 if prec == "c128" else 1e-4
         assert np.max(np.abs(r.pops - _oracle_pops(g, omega, rho0, t0, steps))) <= tol
+
+
+def test_server_concurrent_small_batches_of_mixed_sizes():
+    """Many small walks of different sizes through 4 workers with small batches:
+    concurrent batched launches with different shared-memory sizes must all
+    succeed (the small-walk kernel's limit is shared by every stream) and match
+    the oracle on a sample."""
+    ensure_built()
+    from paper_2003_02450_gb300 import qsw as C
+    rng = np.random.default_rng(12)
+    reqs = []
+    for k in range(96):
+        n = int(rng.choice([6, 11, 17, 24, 31, 40]))
+        g = W.erdos_renyi_mean_degree(n, 3.0, 7000 + k)
+        prec = "c64" if k % 2 else "c128"
+        r = C.Request(g, 0.4, 0.0, 0.1, int(rng.integers(2, 30)), prec, populations=np.eye(n)[0])
+        r.meta = (g, 0.4, W.basis_state(n, 0), 0.0, prec)
+        reqs.append(r)
+    srv = C.qsw_server_create(0, workers=4, max_batch=3, memory_budget_bytes=256e6)
+    try:
+        for r in reqs:
+            C.qsw_server_submit(srv, r)
+        for r in reqs:
+            C.qsw_server_wait(srv, r, 300.0)
+    finally:
+        C.qsw_server_destroy(srv)
+    for r in reqs[:6]:
+        g, omega, rho0, t0, prec = r.meta
+        ref = _oracle_pops(g, omega, rho0, t0, r.c.steps)
+        tol = 1e-10 if prec == "c128" else 1e-4
+        assert np.max(np.abs(r.pops - ref)) <= tol
