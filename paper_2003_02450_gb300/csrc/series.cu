@@ -718,12 +718,21 @@ int choose_tpr(double avg_row) {
 
 void upload_theta_batch();
 
+// The theta tables live in __constant__ memory, one copy per device: they are
+// written once per device (the first context on it), so that contexts created
+// later (e.g. a server's workers) never rewrite them under running kernels.
 void upload_theta(int device) {
-  (void)device;
+  static std::mutex mu;
+  static bool done[64] = {};
+  QSW_CHECK_ARG(device >= 0 && device < 64, QSW_ERR_INVALID_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[device]) return;
   upload_theta_batch();
   QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta, theta_table(QSW_C128), sizeof(double) * kMMax, 0));
   QSW_CUDA_TRY(cudaMemcpyToSymbol(c_theta, theta_table(QSW_C64_BULK), sizeof(double) * kMMax,
                                   sizeof(double) * kMMax));
+  QSW_CUDA_TRY(cudaDeviceSynchronize());   // the tables are in place before any launch
+  done[device] = true;
 }
 
 template <class R> MfOp<R> make_mf(const Op& op, bool adjoint) {
