@@ -1,5 +1,6 @@
-"""A small object API over the C ABI, shaped like the paper's `LQSW` walk
-class (Section 4): build the superoperator once, set an initial state, then
+"""A small object API over the C ABI, shaped like the paper's walk classes
+(Section 4: `LQSW`, `GQSW`, and the GQSW with vertex subspaces for the
+non-moralising walk): build the operator once, set an initial state, then
 `step` / `series`, and read populations.  PyTorch supplies device memory and
 the CUDA stream; the computation is the library's.
 """
@@ -34,24 +35,22 @@ class Context:
             pass
 
 
-class LQSW:
-    """An L-QSW on a digraph G (row = destination, column = source)."""
+class _Walk:
+    """What every walk object shares: one operator handle and its state dimension."""
 
-    def __init__(self, G, omega: float, H=None, sources=(), sinks=(), precision: str = "c128",
-                 ctx: Context | None = None, operator: str = "matfree"):
+    def _init(self, ctx: Context | None, precision: str, omega: float):
         self.ctx = ctx or Context()
         self.precision = precision
-        self.operator = operator
-        self.op = _c.qsw_build_superoperator(self.ctx.handle, G, H, omega, sources, sinks,
-                                             precision, operator)
+        self.omega = omega
+        self.rho0 = None
+        self.last_stats: dict = {}
+
+    def _info(self):
         info = _c.qsw_op_info(self.ctx.handle, self.op)
         self.n_tilde = info["n_tilde"]
         self.n = info["n"]
         self.nnz = info["nnz"]
         self.norms = info["norms"]
-        self.omega = omega
-        self.rho0 = None
-        self.last_stats: dict = {}
 
     @property
     def _dev(self):
@@ -59,8 +58,8 @@ class LQSW:
 
     def set_omega(self, omega: float) -> None:
         _c.qsw_set_omega(self.ctx.handle, self.op, omega)
-        info = _c.qsw_op_info(self.ctx.handle, self.op)
-        self.nnz, self.norms, self.omega = info["nnz"], info["norms"], omega
+        self._info()
+        self.omega = omega
 
     def initial_state(self, rho0=None, populations=None) -> torch.Tensor:
         state = torch.empty(self.n, dtype=torch.complex128, device=self._dev)
@@ -93,15 +92,16 @@ class LQSW:
         _c.qsw_populations(self.ctx.handle, self.op, states, states.shape[0], p)
         return p
 
-    def export_csr(self):
-        rowptr = torch.empty(self.n + 1, dtype=torch.int32, device=self._dev)
-        col = torch.empty(max(1, self.nnz), dtype=torch.int32, device=self._dev)
-        val = torch.empty(max(1, self.nnz), dtype=torch.complex128, device=self._dev)
-        _c.qsw_op_export_csr(self.ctx.handle, self.op, rowptr, col, val)
-        return rowptr, col[: self.nnz], val[: self.nnz]
+    def survival_time(self, t_end: float, q: int, sink: int, rho0: torch.Tensor | None = None):
+        """Expected survival time: Simpson over 1 - p_sink on q + 1 times of [0, t_end]."""
+        rho0 = self.rho0 if rho0 is None else rho0
+        if rho0 is None:
+            raise ValueError("no initial state")
+        eta, self.last_stats = _c.qsw_survival_time(self.ctx.handle, self.op, rho0, t_end, q, sink)
+        return eta
 
     def close(self):
-        if self.op is not None:
+        if getattr(self, "op", None) is not None:
             _c.qsw_op_destroy(self.op)
             self.op = None
 
@@ -110,6 +110,76 @@ class LQSW:
             self.close()
         except Exception:
             pass
+
+
+class LQSW(_Walk):
+    """An L-QSW on a digraph G (row = destination, column = source)."""
+
+    def __init__(self, G, omega: float, H=None, sources=(), sinks=(), precision: str = "c128",
+                 ctx: Context | None = None, operator: str = "matfree"):
+        self._init(ctx, precision, omega)
+        self.operator = operator
+        self.op = _c.qsw_build_superoperator(self.ctx.handle, G, H, omega, sources, sinks,
+                                             precision, operator)
+        self._info()
+
+    def export_csr(self):
+        rowptr = torch.empty(self.n + 1, dtype=torch.int32, device=self._dev)
+        col = torch.empty(max(1, self.nnz), dtype=torch.int32, device=self._dev)
+        val = torch.empty(max(1, self.nnz), dtype=torch.complex128, device=self._dev)
+        _c.qsw_op_export_csr(self.ctx.handle, self.op, rowptr, col, val)
+        return rowptr, col[: self.nnz], val[: self.nnz]
+
+
+class GQSW(_Walk):
+    """A global-interaction walk (Section 2.5.2): by default the G-QSW of
+    digraph G (L = G, H = Laplacian of G^u); with `Ls` (and optionally `H_rot`)
+    the walk of those explicit operators on G's vertices, H required then."""
+
+    def __init__(self, G, omega: float, H=None, Ls=None, H_rot=None, sources=(), sinks=(),
+                 precision: str = "c128", ctx: Context | None = None):
+        self._init(ctx, precision, omega)
+        if Ls is None and H_rot is None:
+            self.op = _c.qsw_build_gqsw(self.ctx.handle, G, H, omega, sources, sinks, precision)
+        else:
+            if H is None:
+                raise ValueError("explicit Lindblad operators need an explicit H")
+            n = G.n if hasattr(G, "n") else np.asarray(G).shape[0]
+            self.op = _c.qsw_build_global(self.ctx.handle, n, H, list(Ls or []), H_rot, omega,
+                                          sources, sinks, precision)
+        self._info()
+
+
+class NMGQSW(_Walk):
+    """The non-moralising G-QSW of digraph G (Eq. nm_gqsw) on its demoralised
+    vertex copies.  `initial_state(populations=...)` and `vertex_populations`
+    work with the N original vertices (Eq. nm_rho_map); `series` returns the
+    copies' populations, `series_vertices` the vertices'."""
+
+    def __init__(self, G, omega: float, precision: str = "c128", ctx: Context | None = None):
+        self._init(ctx, precision, omega)
+        self.N = G.n if hasattr(G, "n") else np.asarray(G).shape[0]
+        self.op = _c.qsw_build_nm_gqsw(self.ctx.handle, G, omega, precision)
+        self._info()
+        self.vsets = _c.qsw_nm_vsets(self.ctx.handle, self.op, self.N)
+
+    def initial_state(self, rho0=None, populations=None) -> torch.Tensor:
+        if populations is not None and len(populations) == self.N and rho0 is None:
+            state = torch.empty(self.n, dtype=torch.complex128, device=self._dev)
+            _c.qsw_nm_initial_state(self.ctx.handle, self.op, populations, state)
+            self.rho0 = state
+            return state
+        return super().initial_state(rho0=rho0, populations=populations)
+
+    def vertex_populations(self, pops_copies: torch.Tensor) -> torch.Tensor:
+        pops_copies = pops_copies.reshape(-1, self.n_tilde)
+        p = torch.empty((pops_copies.shape[0], self.N), dtype=torch.float64, device=self._dev)
+        _c.qsw_nm_populations(self.ctx.handle, self.op, pops_copies, pops_copies.shape[0], p)
+        return p
+
+    def series_vertices(self, t0: float, dt: float, steps: int, rho0: torch.Tensor | None = None):
+        _, p = self.series(t0, dt, steps, rho0, states=False, pops=True)
+        return self.vertex_populations(p)
 
 
 def walk_from_config(cfg: _w.WalkConfig, ctx: Context | None = None) -> LQSW:
