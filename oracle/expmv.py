@@ -8,7 +8,7 @@ without the trace shift (so eta = 1).  The parameters (m*, s) come from their
 Code Fragment 3.1 using the 1-norm series of A (Section 4 footnote, read as
 ||(tA)^p||_1 = t^p ||A^p||_1, hence d_p(tA) = t d_p(A)).
 
-Readings (listed in DESIGN.md):
+Readings of points the paper leaves open:
 * p_max = 8, m_max = 55, ell = 2 columns in the norm estimator;
 * theta_m for every m = 1..55 (oracle/theta_tables.json);
 * m* is the smallest m reaching the minimum cost, s = max(cost / m*, 1);

@@ -1,6 +1,6 @@
 """GPU path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (written here, derived in the design doc):
+Tolerances:
 * assembly: identical structure after dropping exact zeros; values within
   4 ulp of the largest |entry| (the condensed rule and the Kronecker sums round
   differently);
