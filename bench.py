@@ -214,6 +214,18 @@ def series_traffic():
     return int(m_bytes.group(1))
 
 
+def csr_equivalent(nnz: int, n: int, peak_gbs: float, kernel_ms: float, matvecs: int) -> dict:
+    """Time a CSR SpMV of the same superoperator would need at 100 % of the
+    measured HBM bandwidth (complex128 values, int32 indices, one term read and
+    one written, one output read and written), against the measured time per
+    application of L~ in the series kernel."""
+    b = nnz * (16 + 4) + (n + 1) * 4 + 2 * n * 16 + 2 * n * 16
+    roof_ms = b / (peak_gbs * 1e9) * 1e3
+    per_app = kernel_ms / max(1, matvecs)
+    return {"csr_bytes_per_application": b, "csr_at_hbm_peak_ms": roof_ms,
+            "ms_per_application": per_app, "ratio": roof_ms / per_app}
+
+
 def fp64_peak_tflops():
     mhz = 2070.0
     try:
@@ -358,7 +370,12 @@ def run_ours(args):
                          "kernel_ms": kern_ms,
                          "hbm_view": {"achieved": achieved, "peak": peak, "unit": "GB/s",
                                       "frac": achieved / peak, "peak_source": peak_kind,
-                                      "algorithmic_bytes_per_launch": alg_bytes}},
+                                      "algorithmic_bytes_per_launch": alg_bytes},
+                         # the CSR formulation's bytes per application (matrix +
+                         # row pointers + term read/write + output update) at the
+                         # measured HBM peak, against this kernel's time per application
+                         "csr_equivalent": csr_equivalent(s0["nnz"], n, peak, kern_ms,
+                                                          s0["matvecs"])},
             "csr_operator_series": csr_line,
             "series": {"m_star": s0["m_star"], "s": s0["s"], "outputs_per_block": s0["outputs_per_block"],
                        "matvecs": s0["matvecs"], "bytes_per_matvec": s0["bytes_per_matvec"],
