@@ -789,7 +789,10 @@ __device__ void dispatch_walk(G g, Red& R, const BWalk& W, double tol, double* s
   }
 }
 
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT)
+// 4 blocks per SM (64 registers): the walks' phase 2 is latency-bound on
+// gathers from L2, and twice the resident clusters outweigh the register
+// spills (batch256: 214 -> 180 ms for the series phase).
+__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 4)
 batch_series_kernel(BArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ Red R;
