@@ -388,6 +388,17 @@ qsw_status qsw_batch_survival_time(qsw_ctx* ctx, int32_t count, qsw_op* const* o
                                    const int32_t* q, const int32_t* sink, double* eta,
                                    qsw_batch_stats* stats);
 
+/* --------------------------------------------------------- diagnostics */
+
+/* Exercise the bounded wait of the series kernel's grid barrier (not in the
+ * paper): a cooperative launch in which one block never arrives, so the
+ * others give up after about a second of polling and record the timeout, as a
+ * series would (QSW_ERR_NOT_CONVERGED).  Returns QSW_OK when the timeout was
+ * reported; *seconds (optional) receives the time the launch took.  The
+ * context stays usable.  Errors: INVALID_ARG, CUDA (the timeout was not
+ * reported). */
+qsw_status qsw_probe_wait_limit(qsw_ctx* ctx, double* seconds);
+
 /* ------------------------------------------------------------- serving */
 
 /* A request server (not in the paper): walks of any size, omega, time grid and

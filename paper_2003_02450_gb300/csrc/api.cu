@@ -709,6 +709,15 @@ qsw_status qsw_batch_survival_time(qsw_ctx* ctx, int32_t count, qsw_op* const* o
   });
 }
 
+qsw_status qsw_probe_wait_limit(qsw_ctx* ctx, double* seconds) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr, QSW_ERR_INVALID_ARG, "ctx is NULL");
+    set_device(ctx);
+    const double s = qsw::probe_wait_limit(ctx);
+    if (seconds) *seconds = s;
+  });
+}
+
 qsw_status qsw_theta_table(int32_t precision, double* theta55) {
   return guarded(nullptr, [&] {
     QSW_CHECK_ARG(theta55 != nullptr, QSW_ERR_INVALID_ARG, "theta55 is NULL");

@@ -139,6 +139,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
                 double* d_pops, qsw_series_stats* stats);
 void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int steps,
                         double* d_out, double* d_pops, qsw_series_stats* stats);
+double probe_wait_limit(qsw_ctx* ctx);   // seconds until the bounded wait gave up
 void apply(const Op& op, const double* d_x, double* d_y);
 void populations(const Op& op, const double* d_rho, int count, double* d_pops);
 void initial_state_from_pops(const Op& op, const double* d_pops, double* d_state);

@@ -133,7 +133,7 @@ __device__ __forceinline__ unsigned long long warp_umax(unsigned long long v) {
 // Grid barrier for a cooperative launch (all blocks co-resident).  The wait is
 // bounded: on timeout the block records kErrBarrier and returns false, and so
 // does every later barrier, so all blocks leave the kernel.
-__device__ bool grid_barrier(Ctrl* c) {
+__device__ bool grid_barrier(Ctrl* c, unsigned limit = kSpinLimit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -148,7 +148,7 @@ __device__ bool grid_barrier(Ctrl* c) {
     } else {
       unsigned spins = 0;
       while (*((volatile unsigned*)&c->bar_gen) == gen) {
-        if (*((volatile int*)&c->error) != kErrNone || ++spins > kSpinLimit) {
+        if (*((volatile int*)&c->error) != kErrNone || ++spins > limit) {
           atomicCAS(&c->error, kErrNone, kErrBarrier);
           ok = 0;
           break;
@@ -548,6 +548,14 @@ series_kernel(SeriesArgs a) {
       }
     }
   }
+}
+
+// The bounded wait of grid_barrier, exercised: block `absent` never arrives,
+// so every other block gives up after `limit` polls and records kErrBarrier.
+__global__ void __launch_bounds__(kBlock) barrier_probe_kernel(Ctrl* ctrl, int absent,
+                                                               unsigned limit) {
+  if ((int)blockIdx.x == absent) return;
+  grid_barrier(ctrl, limit);
 }
 
 __global__ void plan_kernel(const double* __restrict__ dp, int prec, double t0, double dt,
@@ -1075,6 +1083,38 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
     stats->hermitian = herm ? 1 : 0;
     stats->kernel_ms = 0.0;
   }
+}
+
+double probe_wait_limit(qsw_ctx* ctx) {
+  cudaStream_t st = ctx->stream;
+  DevBuf ctrl;
+  ctrl.alloc(sizeof(Ctrl));
+  QSW_CUDA_TRY(cudaMemsetAsync(ctrl.p, 0, sizeof(Ctrl), st));
+  int per_sm = 0;
+  QSW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, barrier_probe_kernel, kBlock, 0));
+  const int grid = std::max(2, std::min(per_sm, 1) * ctx->num_sms);
+  Ctrl* c = ctrl.as<Ctrl>();
+  int absent = 0;
+  unsigned limit = 1u << 20;   // ~1 s of polling
+  void* params[] = {&c, &absent, &limit};
+  cudaEvent_t e0, e1;
+  QSW_CUDA_TRY(cudaEventCreate(&e0));
+  QSW_CUDA_TRY(cudaEventCreate(&e1));
+  QSW_CUDA_TRY(cudaEventRecord(e0, st));
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  QSW_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)barrier_probe_kernel, dim3(grid),
+                                           dim3(kBlock), params, 0, st));
+  QSW_CUDA_TRY(cudaEventRecord(e1, st));
+  Ctrl h{};
+  QSW_CUDA_TRY(cudaMemcpyAsync(&h, ctrl.p, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (h.error != kErrBarrier)
+    throw Error{QSW_ERR_CUDA, "barrier probe: the bounded wait did not report its timeout"};
+  return ms * 1e-3;
 }
 
 void apply(const Op& op, const double* d_x, double* d_y) {

@@ -130,6 +130,7 @@ _SIGNATURES = {
     "qsw_batch_survival_time": ([c_void_p, c_int32, POINTER(c_void_p), POINTER(c_void_p),
                                  POINTER(c_double), POINTER(c_int32), POINTER(c_int32),
                                  POINTER(c_double), POINTER(qsw_batch_stats)], c_int32),
+    "qsw_probe_wait_limit": ([c_void_p, POINTER(c_double)], c_int32),
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
     "qsw_kernel_launches": ([], c_int64),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
@@ -416,6 +417,13 @@ def qsw_batch_survival_time(ctx, ops, d_rho0s, t_ends, qs, sinks):
         (c_double * k)(*[float(x) for x in t_ends]), (c_int32 * k)(*[int(x) for x in qs]),
         (c_int32 * k)(*[int(x) for x in sinks]), eta, byref(stats)), ctx)
     return list(eta), stats.as_dict()
+
+
+def qsw_probe_wait_limit(ctx) -> float:
+    """Run the grid barrier with one block absent; seconds until it gave up."""
+    sec = c_double()
+    _check(lib().qsw_probe_wait_limit(ctx, byref(sec)), ctx)
+    return sec.value
 
 
 def qsw_server_create(device: int = 0, workers: int = 2, max_batch: int = 64,
