@@ -38,8 +38,6 @@ template <class R> struct MfOp {
                        // by mf_partA2), 0: natural order (part A row by row)
 };
 
-template <class T> __device__ __forceinline__ T ldcg_t(const T* p) { return __ldcg(p); }
-
 // Reads of the operand x.  Inside the persistent series kernel x was written
 // by other SMs before the last grid (or cluster) barrier, whose fences form a
 // gpu-scope (cluster-scope) release/acquire pair with those writes; a weak
