@@ -307,19 +307,36 @@ void upload(DevBuf& b, const std::vector<T>& h, cudaStream_t st) {
     QSW_CUDA_TRY(cudaMemcpyAsync(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice, st));
 }
 
-int read_int(const int* d, cudaStream_t st) {
-  int v = 0;
-  QSW_CUDA_TRY(cudaMemcpyAsync(&v, d, sizeof(int), cudaMemcpyDeviceToHost, st));
-  QSW_CUDA_TRY(cudaStreamSynchronize(st));
-  return v;
-}
-
-// cnt[0..n) -> rowptr[0..n]; returns the total.
-int scan_counts(DevBuf& cnt, DevBuf& rowptr, int n, cudaStream_t st) {
+// cnt[0..n) -> rowptr[0..n] on the device.  The totals that size the
+// following allocations are known on the host (see the callers), so the build
+// issues its kernels without waiting for read-backs.
+void scan_counts(DevBuf& cnt, DevBuf& rowptr, int n, cudaStream_t st) {
   rowptr.alloc(sizeof(int) * (n + 1));
   QSW_LAUNCH scan_small_kernel<<<1, 1024, 0, st>>>(cnt.as<int>(), rowptr.as<int>(), n);
   QSW_CUDA_TRY(cudaGetLastError());
-  return read_int(rowptr.as<int>() + n, st);
+}
+
+// Off-diagonal entries of G^u = max(G, G^T) (union_count_kernel's total):
+// rows of G and of its transpose merged, counting distinct columns.  O(nnz).
+int undirected_offdiag(int N, const std::vector<int>& rowptr, const std::vector<int>& col) {
+  std::vector<int> tr(N + 1, 0), tc(col.size());
+  for (int c : col) ++tr[c + 1];
+  for (int i = 0; i < N; ++i) tr[i + 1] += tr[i];
+  std::vector<int> fill(tr.begin(), tr.end() - 1);
+  for (int i = 0; i < N; ++i)
+    for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) tc[fill[col[e]]++] = i;   // rows in order
+  long long total = 0;
+  for (int i = 0; i < N; ++i) {
+    int a = rowptr[i], b = tr[i];
+    while (a < rowptr[i + 1] || b < tr[i + 1]) {
+      const int ca = a < rowptr[i + 1] ? col[a] : INT_MAX;
+      const int cb = b < tr[i + 1] ? tc[b] : INT_MAX;
+      if (ca <= cb) ++a;
+      if (cb <= ca) ++b;
+      ++total;
+    }
+  }
+  return (int)total;
 }
 
 }  // namespace
@@ -347,7 +364,7 @@ void build_graph(Op& op) {
   if (g.nnz_g)
     QSW_LAUNCH count_cols_kernel<<<grid_for(g.nnz_g, 256, 4096), 256, 0, st>>>(g.nnz_g, g.g_col.as<int>(),
                                                                      g.scratch.as<int>());
-  scan_counts(g.scratch, g.gt_rowptr, N, st);
+  scan_counts(g.scratch, g.gt_rowptr, N, st);   // total: nnz(G)
   g.gt_col.alloc(sizeof(int) * (g.nnz_g + 1));
   g.gt_w.alloc(sizeof(double) * (g.nnz_g + 1));
   QSW_CUDA_TRY(cudaMemcpyAsync(g.scratch.p, g.gt_rowptr.p, sizeof(int) * N,
@@ -366,7 +383,8 @@ void build_graph(Op& op) {
     QSW_LAUNCH union_count_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
         N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.gt_rowptr.as<int>(), g.gt_col.as<int>(),
         g.scratch.as<int>());
-    g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    g.nnz_hoff = undirected_offdiag(N, op.g_rowptr, op.g_col);
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
     QSW_LAUNCH laplacian_fill_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
@@ -380,13 +398,16 @@ void build_graph(Op& op) {
     upload(hw, op.h_w, st);
     QSW_LAUNCH h_offcount_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(N, hr.as<int>(), hc.as<int>(),
                                                                g.scratch.as<int>());
-    g.nnz_hoff = scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    scan_counts(g.scratch, g.hoff_rowptr, N, st);
+    g.nnz_hoff = 0;   // h_offcount_kernel's total: entries off the diagonal
+    for (int i = 0; i < N; ++i)
+      for (int e = op.h_rowptr[i]; e < op.h_rowptr[i + 1]; ++e) g.nnz_hoff += op.h_col[e] != i;
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
     QSW_LAUNCH h_split_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
         N, hr.as<int>(), hc.as<int>(), hw.as<double>(), g.hoff_rowptr.as<int>(),
         g.hoff_col.as<int>(), g.hoff_val.as<double>(), g.hdiag.as<double>());
-    QSW_CUDA_TRY(cudaStreamSynchronize(st));   // hr/hc/hw die at scope exit
+    // hr/hc/hw are freed in stream order after h_split_kernel
   }
   QSW_CUDA_TRY(cudaGetLastError());
 }
@@ -398,6 +419,9 @@ void build_jumps(Op& op) {
   const int graph_on = op.omega > 0.0;
   PortArgs pa{g.N, Nt, g.n_src, g.n_snk, g.src_v.as<int>(), g.src_r.as<double>(),
               g.snk_v.as<int>(), g.snk_r.as<double>()};
+  // jump_count_kernel's total, either direction: one jump per arc when the
+  // graph terms are on, plus one per port
+  const int total = (graph_on ? g.nnz_g : 0) + g.n_src + g.n_snk;
   for (int adjoint = 0; adjoint < 2; ++adjoint) {
     DevBuf& rp = adjoint ? g.jt_rowptr : g.j_rowptr;
     DevBuf& cl = adjoint ? g.jt_col : g.j_col;
@@ -408,7 +432,7 @@ void build_jumps(Op& op) {
     QSW_LAUNCH jump_count_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, grow,
                                                                g.scratch.as<int>(), adjoint);
     QSW_CUDA_TRY(cudaGetLastError());
-    const int total = scan_counts(g.scratch, rp, Nt, st);
+    scan_counts(g.scratch, rp, Nt, st);
     cl.alloc(sizeof(int) * (total + 1));
     vl.alloc(sizeof(double) * (total + 1));
     QSW_LAUNCH jump_fill_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(pa, graph_on, op.omega, grow, gcol,
@@ -416,7 +440,7 @@ void build_jumps(Op& op) {
                                                               vl.as<double>(), adjoint);
     QSW_CUDA_TRY(cudaGetLastError());
   }
-  g.n_jumps = read_int(g.j_rowptr.as<int>() + Nt, st);
+  g.n_jumps = total;
   g.dtot.alloc(sizeof(double) * Nt);
   QSW_LAUNCH row_sum_kernel<<<grid_for(Nt, 128, 4096), 128, 0, st>>>(Nt, g.jt_rowptr.as<int>(),
                                                           g.jt_val.as<double>(), g.dtot.as<double>());
