@@ -176,18 +176,23 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
  * its graph, Hamiltonian and ports (the package's set_omega, Section 4). */
 qsw_status qsw_set_omega(qsw_op* op, double omega);
 
-/* Sizes and norms of an operator.  norms[0] = ||L~||_1 (exact), norms[p-1] =
- * estimate of ||L~^p||_1 for p = 2..9.  Any output pointer may be NULL. */
+/* Sizes and norms of an operator.  norms[0] = ||L~||_1 (exact; for a global
+ * walk exact when it has one Lindblad operator without diagonal entries, else
+ * estimated), norms[p-1] = estimate of ||L~^p||_1 for p = 2..9.  n_tilde is the
+ * state dimension N~ (the vertex copies for an NM-G-QSW), n = N~^2.  Any
+ * output pointer may be NULL; asking for the norms of an operator built with
+ * QSW_BUILD_DEFER_NORMS computes them. */
 qsw_status qsw_op_info(const qsw_op* op, int64_t* n_tilde, int64_t* n, int64_t* nnz,
                        double* norms9);
 /* nnz is the number of stored entries of the CSR form of L~ (computed from the
- * structure without assembling it). */
+ * structure without assembling it); 0 for global-interaction walks, which have
+ * no CSR form. */
 
 /* Copy the CSR of L~ (assembled on first use for a matrix-free operator) into
  * caller device buffers: d_rowptr[n + 1],
  * d_col[nnz], d_val[2 nnz] (complex128; for a QSW_C64_BULK operator its
  * complex64 values are widened).  Any pointer may be NULL to skip that array.
- * Used by tests and tools. */
+ * Used by tests and tools.  Errors: INVALID_ARG for global-interaction walks. */
 qsw_status qsw_op_export_csr(const qsw_op* op, int32_t* d_rowptr, int32_t* d_col,
                              double* d_val);
 
