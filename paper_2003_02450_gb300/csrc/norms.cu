@@ -14,10 +14,26 @@
 // follows the algorithm's branches on the few scalars each iteration returns.
 // All reductions use a fixed grid and a fixed summation order, so repeated
 // builds give bit-identical estimates.
+//
+// Work shared between the estimates (same values, fewer products):
+//   * the first iteration of every estimate starts from the same block X0, so
+//     A^p X0 for p = 1..9 is one chain;
+//   * later iterations start from unit vectors e_c, and the estimates for
+//     successive p often pick the same c: A^k e_c is kept per c and extended,
+//     so A^p e_c costs p - k products instead of p;
+//   * for the matrix-free L-QSW operator A^k e_c is zero outside a box of rows
+//     x columns that grows by one H-neighbourhood per product; the products
+//     visit only that box (the elements they compute are the ones the full
+//     product computes, in the same order);
+//   * on graphs where that box stays small (lattices), the adjoint step takes
+//     (A^H)^p sign(Y) = (A^H)^p 1 + (A^H)^p (sign(Y) - 1): the first term is one
+//     chain shared by every estimate, the second is supported on the box of Y.
+//     This one changes the rounding of Z (not its value in exact arithmetic).
 #include <math.h>
 
 #include <algorithm>
 
+#include "matfree.cuh"
 #include "op.h"
 
 namespace qsw {
@@ -275,35 +291,342 @@ __global__ void roots_kernel(const double* __restrict__ norms, double* __restric
   }
 }
 
+// ---------------------------------------------- supports of unit-vector chains
+// A vector supported on rows I x columns J of the N~ x N~ density matrix maps
+// under L~ (or L~^H) to one supported on I' x J':
+//   I' = I + {i : row i of H meets I} + T,   J' = J + {j : row j of H meets J} + T,
+// T = {v : a jump into (v, v) starts at some q in I and J}: part A of C at (i, j)
+// reads x(m, j) for m in row i of H, part B reads x(i, m) for m in row j, the
+// diagonal term reads x(i, j), and the jump sum at (v, v) reads x(q, q).
+// Masks hold [2 Nt] bytes (rows, then columns); lists hold [2 Nt] ints (rows,
+// then columns, ascending) and count[0] = |I|, count[1] = |J|.
+__global__ void box_grow_kernel(MfOp<double> op, const unsigned char* __restrict__ in,
+                                unsigned char* __restrict__ out) {
+  const int Nt = op.Nt;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < Nt; v += gridDim.x * blockDim.x) {
+    bool r = in[v] != 0, c = in[Nt + v] != 0;
+    if (v < op.N)
+      for (int e = op.hrow[v]; e < op.hrow[v + 1]; ++e) {
+        const int m = op.hcol[e];
+        r = r || in[m] != 0;
+        c = c || in[Nt + m] != 0;
+      }
+    for (int e = op.jrow[v]; e < op.jrow[v + 1]; ++e) {
+      const int q = op.jcol[e];
+      if (in[q] && in[Nt + q]) r = c = true;
+    }
+    out[v] = r;
+    out[Nt + v] = c;
+  }
+}
+
+constexpr int kListThreads = 1024;
+
+// Both masks to ascending index lists (one block, chunks of kListThreads).
+__global__ void __launch_bounds__(kListThreads)
+box_list_kernel(int Nt, const unsigned char* __restrict__ mask, int* __restrict__ list,
+                int* __restrict__ count) {
+  __shared__ int warp_tot[kListThreads / 32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int s = 0; s < 2; ++s) {
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < Nt; c0 += kListThreads) {
+      const int v = c0 + threadIdx.x;
+      const bool f = v < Nt && mask[s * Nt + v] != 0;
+      const unsigned b = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) warp_tot[w] = __popc(b);
+      __syncthreads();
+      int off = base;
+      for (int q = 0; q < w; ++q) off += warp_tot[q];
+      if (f) list[s * Nt + off + __popc(b & ((1u << lane) - 1u))] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int q = 0; q < kListThreads / 32; ++q) tot += warp_tot[q];
+        base += tot;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) count[s] = base;
+    __syncthreads();
+  }
+}
+
+// Start of a chain: e_idx, idx = a + Nt b (row a, column b).  The masks and
+// the vector are zero on entry.
+__global__ void box_init_kernel(int Nt, int a, int b, unsigned char* __restrict__ mask,
+                                int* __restrict__ list, int* __restrict__ count,
+                                double2* __restrict__ v) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    mask[a] = 1;
+    mask[Nt + b] = 1;
+    list[0] = a;
+    list[Nt] = b;
+    count[0] = 1;
+    count[1] = 1;
+    v[a + (long long)Nt * b] = make_double2(1.0, 0.0);
+  }
+}
+
+constexpr int kBoxBlock = 256;
+constexpr int kBoxWarps = kBoxBlock / 32;
+
+// y = L~ x (or L~^H x) on the box (list, count) of the output; y is left as it
+// is outside the box.  Blocks take the box's columns, warps 64-row chunks of
+// its rows.  Every element is computed by the same helpers, in the same order,
+// as in the full product: with all rows in the box the chunks are the
+// operator's paired 64-row windows, otherwise the rows run through part B and
+// then their own part-A loops.
+template <bool ADJ>
+__global__ void __launch_bounds__(kBoxBlock)
+mf_box_kernel(MfOp<double> op, const int* __restrict__ list, const int* __restrict__ count,
+              const double2* __restrict__ x, double2* __restrict__ y) {
+  const int nI = count[0], nJ = count[1];
+  const int* rows = list;
+  const int* cols = list + op.Nt;
+  const bool all_rows = nI == op.Nt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jj = blockIdx.x; jj < nJ; jj += gridDim.x) {
+    const int j = cols[jj];
+    for (int i0 = warp * kItemRows; i0 < nI; i0 += kBoxWarps * kItemRows) {
+      int irow[2];
+      double ox[2], oy[2];
+      if (all_rows) {
+        mf_window_rows(op.prow, i0, lane, op.Nt - 1, irow);
+        mf_window_apply<double, double2, ADJ>(op, x, j, i0, irow, ox, oy);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+          const int k = i0 + lane + 32 * u;
+          irow[u] = k < nI ? rows[k] : -1;
+        }
+        double cx[2], cy[2];
+        mf_partB<double, double2, 2>(op, x, j, irow, cx, cy);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+          if (irow[u] >= 0)
+            mf_finish<double, double2, ADJ>(op, x, irow[u], j, cx[u], cy[u], ox[u], oy[u]);
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u)
+        if (irow[u] >= 0) y[irow[u] + (long long)op.Nt * j] = make_double2(ox[u], oy[u]);
+    }
+  }
+}
+
+// D = sign(Y) - 1 on the box of Y (0 where Y = 0); D is zero outside the box.
+__global__ void sign_minus_one_kernel(int Nt, const int* __restrict__ list,
+                                      const int* __restrict__ count, const double2* __restrict__ Y,
+                                      double2* __restrict__ D) {
+  const int nI = count[0];
+  const long long tot = (long long)nI * count[1];
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long k = list[e % nI] + (long long)Nt * list[Nt + e / nI];
+    const double2 y = Y[k];
+    const double a = cabs(y);
+    D[k] = a == 0.0 ? make_double2(0.0, 0.0) : make_double2(y.x / a - 1.0, y.y / a);
+  }
+}
+
+__global__ void fill_ones_kernel(long long n, double2* __restrict__ v) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    v[e] = make_double2(1.0, 0.0);
+}
+
+// z = a + b
+__global__ void add_kernel(long long n, const double2* __restrict__ a, const double2* __restrict__ b,
+                           double2* __restrict__ z) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const double2 u = a[e], v = b[e];
+    z[e] = make_double2(u.x + v.x, u.y + v.y);
+  }
+}
+
+// A^pow e_idx (or, for the adjoint step, (A^H)^pow D), with a spare vector;
+// both are zero outside the current box.  Each product writes a box that
+// contains the previous two, so the spare needs no clearing between products.
+struct Chain {
+  int idx = -1;
+  int pow = 0;
+  long long used = 0;
+  bool box = false;         // support tracked (matrix-free L-QSW operator)
+  bool full = false;        // the box is the whole matrix (known on the host)
+  long long box_elems = 0;  // |I| |J| at the last host read
+  DevBuf v, w, mask, mask2, list, count;
+};
+
+constexpr int kChainsMax = 8;
+constexpr size_t kChainBytes = size_t(1) << 30;   // device memory for cached chains
+constexpr size_t kOnesChainBytes = size_t(4) << 30;
+
 struct Estimator {
   cudaStream_t st;
   int n, t;
+  int Nt = 0;
   const Op* op;
   const Csr* A;    // CSR operator, or null for matrix-free
   const Csr* AH;
   DevBuf X, Y, W, h, partials, pv, pi, out;
+  bool box_ok = false;      // matrix-free L-QSW: unit chains track their box
+  bool split_ok = false;    // ... and the adjoint step may split off (A^H)^p 1
+  Chain chains[kChainsMax];
+  int n_chains = 2;
+  long long tick = 0;
+  Chain dchain;             // (A^H)^q D of the split adjoint step
+  DevBuf ones;              // [(kNormPowers + 1) n]: (A^H)^k 1, k = 0..ones_pow
+  int ones_pow = -1;
 
   void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
 
-  void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp) {
-    // out = M^p in (M = L or L^H), ping-ponging through tmp
+  void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols) {
+    // out = M^p in (M = L or L^H) for `cols` columns, ping-ponging through tmp
     const double2* src = in;
     for (int k = 0; k < p; ++k) {
       double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
       if (A) {
         const Csr& M = adjoint ? *AH : *A;
         QSW_LAUNCH spmm_kernel<<<grid_for((long long)n * 8, 256, 152 * 16), 256, 0, st>>>(
-            n, t, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
+            n, cols, M.rowptr.as<int>(), M.col.as<int>(), M.val.as<double2>(), src, dst);
       } else if (op->gq.active) {
-        gq_apply64(*op, adjoint, t, reinterpret_cast<const double*>(src),
+        gq_apply64(*op, adjoint, cols, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), 1.0);
       } else {
-        mf_apply64(*op, adjoint, t, reinterpret_cast<const double*>(src),
+        mf_apply64(*op, adjoint, cols, reinterpret_cast<const double*>(src),
                    reinterpret_cast<double*>(dst), 1.0);
       }
       src = dst;
     }
     QSW_CUDA_TRY(cudaGetLastError());
+  }
+
+  // One product of a chain: on its box (grown first), or the full product.
+  void chain_step(Chain& ch, bool adjoint) {
+    if (ch.box && !ch.full) {
+      const MfOp<double> m = make_mf<double>(*op, adjoint);
+      QSW_LAUNCH box_grow_kernel<<<grid_for(Nt, 256, 1024), 256, 0, st>>>(
+          m, ch.mask.as<unsigned char>(), ch.mask2.as<unsigned char>());
+      QSW_LAUNCH box_list_kernel<<<1, kListThreads, 0, st>>>(Nt, ch.mask2.as<unsigned char>(),
+                                                             ch.list.as<int>(), ch.count.as<int>());
+      const unsigned grid = (unsigned)std::min(Nt, 152 * 8);
+      if (adjoint)
+        QSW_LAUNCH mf_box_kernel<true><<<grid, kBoxBlock, 0, st>>>(
+            m, ch.list.as<int>(), ch.count.as<int>(), ch.v.as<double2>(), ch.w.as<double2>());
+      else
+        QSW_LAUNCH mf_box_kernel<false><<<grid, kBoxBlock, 0, st>>>(
+            m, ch.list.as<int>(), ch.count.as<int>(), ch.v.as<double2>(), ch.w.as<double2>());
+      QSW_CUDA_TRY(cudaGetLastError());
+      std::swap(ch.mask, ch.mask2);
+    } else {
+      mult(adjoint, 1, ch.v.as<double2>(), ch.w.as<double2>(), nullptr, 1);
+    }
+    std::swap(ch.v, ch.w);
+    ++ch.pow;
+  }
+
+  void read_box(Chain& ch) {
+    int c[2] = {0, 0};
+    QSW_CUDA_TRY(cudaMemcpyAsync(c, ch.count.p, sizeof(c), cudaMemcpyDeviceToHost, st));
+    sync();
+    ch.box_elems = (long long)c[0] * c[1];
+    ch.full = c[0] == Nt && c[1] == Nt;
+  }
+
+  // Both vectors (and the masks) cleared; the box, when tracked, still empty.
+  void chain_reset(Chain& ch, bool with_box) {
+    const size_t vb = sizeof(double2) * (size_t)n;
+    ch.v.alloc(vb);
+    ch.w.alloc(vb);
+    QSW_CUDA_TRY(cudaMemsetAsync(ch.v.p, 0, vb, st));
+    QSW_CUDA_TRY(cudaMemsetAsync(ch.w.p, 0, vb, st));
+    ch.box = with_box;
+    ch.full = false;
+    ch.pow = 0;
+    ch.box_elems = 0;
+    if (with_box) {
+      ch.mask.alloc(2 * (size_t)Nt);
+      ch.mask2.alloc(2 * (size_t)Nt);
+      ch.list.alloc(sizeof(int) * 2 * (size_t)Nt);
+      ch.count.alloc(sizeof(int) * 2);
+      QSW_CUDA_TRY(cudaMemsetAsync(ch.mask.p, 0, 2 * (size_t)Nt, st));
+    }
+  }
+
+  // dst = A^p e_idx, from the chain kept for idx (extended as needed); the
+  // chain is returned (its box describes the support of dst).
+  Chain* unit_power(int idx, int p, double2* dst) {
+    Chain* ch = nullptr;
+    for (int q = 0; q < n_chains; ++q)
+      if (chains[q].idx == idx) ch = &chains[q];
+    if (ch && ch->pow > p) ch->idx = -1;   // cannot go back: restart it
+    if (!ch || ch->idx != idx) {
+      if (!ch) {   // an unused slot, else the least recently used
+        ch = &chains[0];
+        for (int q = 1; q < n_chains; ++q)
+          if ((chains[q].idx < 0) != (ch->idx < 0) ? chains[q].idx < 0 : chains[q].used < ch->used)
+            ch = &chains[q];
+      }
+      ch->idx = idx;
+      chain_reset(*ch, box_ok);
+      if (box_ok)
+        QSW_LAUNCH box_init_kernel<<<1, 32, 0, st>>>(Nt, idx % Nt, idx / Nt,
+                                                     ch->mask.as<unsigned char>(),
+                                                     ch->list.as<int>(), ch->count.as<int>(),
+                                                     ch->v.as<double2>());
+      else
+        QSW_LAUNCH set_units_kernel<<<1, 32, 0, st>>>(n, 1, ch->v.as<double2>(), idx, 0);
+      QSW_CUDA_TRY(cudaGetLastError());
+    }
+    ch->used = ++tick;
+    const bool advanced = ch->pow < p;
+    while (ch->pow < p) chain_step(*ch, false);
+    QSW_CUDA_TRY(cudaMemcpyAsync(dst, ch->v.p, sizeof(double2) * (size_t)n,
+                                 cudaMemcpyDeviceToDevice, st));
+    if (ch->box && !ch->full && advanced) read_box(*ch);
+    return ch;
+  }
+
+  // ones[k n ..] = (A^H)^k 1 for k = 0..p (the all-ones vector and its chain).
+  void ensure_ones(int p) {
+    const size_t nn = (size_t)n;
+    if (ones_pow < 0) {
+      ones.alloc(sizeof(double2) * nn * (kNormPowers + 1));
+      QSW_LAUNCH fill_ones_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, ones.as<double2>());
+      QSW_CUDA_TRY(cudaGetLastError());
+      ones_pow = 0;
+    }
+    for (; ones_pow < p; ++ones_pow)
+      mult(true, 1, ones.as<double2>() + nn * ones_pow, ones.as<double2>() + nn * (ones_pow + 1),
+           nullptr, 1);
+  }
+
+  // Y(:, c) <- (A^H)^p sign(Y(:, c)) = (A^H)^p 1 + (A^H)^p D_c, D_c = sign(Y(:, c)) - 1
+  // supported on the box of the chain that produced Y(:, c).
+  void adjoint_split(int p, Chain* const* src) {
+    ensure_ones(p);
+    double2* Yp = Y.as<double2>();
+    const size_t nn = (size_t)n;
+    for (int c = 0; c < t; ++c) {
+      Chain& d = dchain;
+      chain_reset(d, true);
+      QSW_CUDA_TRY(cudaMemcpyAsync(d.mask.p, src[c]->mask.p, 2 * (size_t)Nt,
+                                   cudaMemcpyDeviceToDevice, st));
+      QSW_CUDA_TRY(cudaMemcpyAsync(d.list.p, src[c]->list.p, sizeof(int) * 2 * (size_t)Nt,
+                                   cudaMemcpyDeviceToDevice, st));
+      QSW_CUDA_TRY(cudaMemcpyAsync(d.count.p, src[c]->count.p, sizeof(int) * 2,
+                                   cudaMemcpyDeviceToDevice, st));
+      QSW_LAUNCH sign_minus_one_kernel<<<grid_for(src[c]->box_elems, 256, 4096), 256, 0, st>>>(
+          Nt, d.list.as<int>(), d.count.as<int>(), Yp + nn * c, d.v.as<double2>());
+      QSW_CUDA_TRY(cudaGetLastError());
+      for (int q = 0; q < p; ++q) chain_step(d, true);
+      QSW_LAUNCH add_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(
+          n, ones.as<double2>() + nn * p, d.v.as<double2>(), Yp + nn * c);
+      QSW_CUDA_TRY(cudaGetLastError());
+    }
   }
 
   void colnorms(const double2* Yp, double* host2) {
@@ -339,7 +662,7 @@ struct Estimator {
     double2* c0 = chain.as<double2>();
     QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, c0);
     QSW_CUDA_TRY(cudaGetLastError());
-    for (int p = 1; p <= pmax; ++p) mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr);
+    for (int p = 1; p <= pmax; ++p) mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr, t);
   }
 
   double estimate(int p) {
@@ -350,12 +673,13 @@ struct Estimator {
     double est_old = 0.0, est = 0.0;
     int ind[2] = {0, 0};
     int ind_best = 0;
+    Chain* ych[2] = {nullptr, nullptr};   // chains behind the columns of Y (k >= 2)
     for (int k = 1;; ++k) {
       if (k == 1)
         QSW_CUDA_TRY(cudaMemcpyAsync(Yp, chain.as<double2>() + (size_t)n * t * p,
                                      sizeof(double2) * (size_t)n * t, cudaMemcpyDeviceToDevice, st));
-      else
-        mult(false, p, Xp, Yp, Wp);
+      else   // Y = A^p [e_ind0, e_ind1]
+        for (int c = 0; c < t; ++c) ych[c] = unit_power(ind[c], p, Yp + (size_t)n * c);
       double cn[2] = {0, 0};
       colnorms(Yp, cn);
       const int jbest = (t > 1 && cn[1] > cn[0]) ? 1 : 0;
@@ -367,8 +691,17 @@ struct Estimator {
       }
       est_old = est;
       if (k > kItMax) break;
-      QSW_LAUNCH sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>((long long)n * t, Yp, Xp);
-      mult(true, p, Xp, Yp, Wp);   // Z = (A^H)^p S, in Y
+      // Z = (A^H)^p S, S = sign(Y), in Y
+      bool split = k >= 2 && split_ok;
+      for (int c = 0; c < t && split; ++c)
+        split = ych[c]->box && !ych[c]->full && ych[c]->box_elems * 16 <= (long long)n;
+      if (split) {
+        adjoint_split(p, ych);
+      } else {
+        QSW_LAUNCH sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>(
+            (long long)n * t, Yp, Xp);
+        mult(true, p, Xp, Yp, Wp, t);
+      }
       QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
       QSW_CUDA_TRY(cudaGetLastError());
       double hmax, hbest;
@@ -394,9 +727,6 @@ struct Estimator {
       }
       ind[0] = fresh[0];
       ind[1] = fresh[1];
-      QSW_CUDA_TRY(cudaMemsetAsync(Xp, 0, sizeof(double2) * (size_t)n * t, st));
-      QSW_LAUNCH set_units_kernel<<<1, 32, 0, st>>>(n, t, Xp, ind[0], ind[1] < 0 ? 0 : ind[1]);
-      QSW_CUDA_TRY(cudaGetLastError());
       hist.push_back(ind[0]);
       if (t > 1) hist.push_back(ind[1]);
     }
@@ -448,6 +778,12 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.pv.alloc(sizeof(double) * kRedGrid);
   E.pi.alloc(sizeof(int) * kRedGrid);
   E.out.alloc(sizeof(double) * 4);
+  E.Nt = op.Nt;
+  E.box_ok = !L && !op.gq.active;
+  E.split_ok = E.box_ok &&
+               sizeof(double2) * (size_t)n * (kNormPowers + 1) <= kOnesChainBytes;
+  E.n_chains = (int)std::min<size_t>(
+      kChainsMax, std::max<size_t>(2, kChainBytes / (2 * sizeof(double2) * (size_t)n)));
   if (one_estimated) {   // several sandwich operators (or diagonal entries): estimate p = 1 too
     E.make_chain(kNormPowers);
     one = E.estimate(1);
