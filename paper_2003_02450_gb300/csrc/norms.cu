@@ -15,7 +15,8 @@
 // All reductions use a fixed grid and a fixed summation order, so repeated
 // builds give bit-identical estimates.
 //
-// Work shared between the estimates (same values, fewer products):
+// Work shared between the estimates (same values up to rounding, fewer
+// products):
 //   * the first iteration of every estimate starts from the same block X0, so
 //     A^p X0 for p = 1..9 is one chain;
 //   * later iterations start from unit vectors e_c, and the estimates for
@@ -27,8 +28,12 @@
 //     product computes, in the same order);
 //   * on graphs where that box stays small (lattices), the adjoint step takes
 //     (A^H)^p sign(Y) = (A^H)^p 1 + (A^H)^p (sign(Y) - 1): the first term is one
-//     chain shared by every estimate, the second is supported on the box of Y.
-//     This one changes the rounding of Z (not its value in exact arithmetic).
+//     chain shared by every estimate, the second is supported on the box of Y;
+//   * L~ and L~^H map X^dag to (L X)^dag: the first column of the starting
+//     block (all ones) is Hermitian, so its products are taken on the upper
+//     triangle and mirrored, and a unit-vector pair e_(a,b), e_(b,a) (the row
+//     ranking ties them) costs one column, the other being its mirror.
+// The last two change the rounding of some products, not their values.
 #include <math.h>
 
 #include <algorithm>
@@ -416,6 +421,38 @@ mf_box_kernel(MfOp<double> op, const int* __restrict__ list, const int* __restri
   }
 }
 
+// y = L~ x (or L~^H x) for a Hermitian x; both maps preserve Hermiticity, so
+// only the upper triangle is computed (the same per-element helpers and order
+// as the full product) and mirrored.  The diagonal's imaginary part, zero in
+// exact arithmetic, is stored as zero, which keeps y exactly Hermitian.  Blocks
+// take the columns longest first (column j holds j + 1 upper-triangle rows).
+template <bool ADJ>
+__global__ void __launch_bounds__(kBoxBlock)
+mf_herm_kernel(MfOp<double> op, const double2* __restrict__ x, double2* __restrict__ y) {
+  const int Nt = op.Nt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int jb = blockIdx.x; jb < Nt; jb += gridDim.x) {
+    const int j = Nt - 1 - jb;
+    for (int i0 = warp * kItemRows; i0 <= j; i0 += kBoxWarps * kItemRows) {
+      int irow[2];
+      double ox[2], oy[2];
+      mf_window_rows(op.prow, i0, lane, j, irow);
+      mf_window_apply<double, double2, ADJ>(op, x, j, i0, irow, ox, oy);
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int i = irow[u];
+        if (i < 0) continue;
+        if (i == j) {
+          y[i + (long long)Nt * j] = make_double2(ox[u], 0.0);
+        } else {
+          y[i + (long long)Nt * j] = make_double2(ox[u], oy[u]);
+          y[j + (long long)Nt * i] = make_double2(ox[u], -oy[u]);
+        }
+      }
+    }
+  }
+}
+
 // D = sign(Y) - 1 on the box of Y (0 where Y = 0); D is zero outside the box.
 __global__ void sign_minus_one_kernel(int Nt, const int* __restrict__ list,
                                       const int* __restrict__ count, const double2* __restrict__ Y,
@@ -428,6 +465,29 @@ __global__ void sign_minus_one_kernel(int Nt, const int* __restrict__ list,
     const double2 y = Y[k];
     const double a = cabs(y);
     D[k] = a == 0.0 ? make_double2(0.0, 0.0) : make_double2(y.x / a - 1.0, y.y / a);
+  }
+}
+
+// out = in^dag for N~ x N~ matrices (column-major), through 32 x 32 tiles.
+__global__ void conj_transpose_kernel(int Nt, const double2* __restrict__ in,
+                                      double2* __restrict__ out) {
+  __shared__ double2 tile[32][33];
+  const int tiles = (Nt + 31) / 32;
+  for (long long b = blockIdx.x; b < (long long)tiles * tiles; b += gridDim.x) {
+    const int bi = (int)(b % tiles) * 32, bj = (int)(b / tiles) * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int i = bi + threadIdx.x, j = bj + r;
+      if (i < Nt && j < Nt) tile[r][threadIdx.x] = in[i + (long long)Nt * j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+      const int i = bj + threadIdx.x, j = bi + r;   // out(i, j) = conj(in(j, i))
+      if (i < Nt && j < Nt) {
+        const double2 v = tile[threadIdx.x][r];
+        out[i + (long long)Nt * j] = make_double2(v.x, -v.y);
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -483,8 +543,26 @@ struct Estimator {
 
   void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
 
-  void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols) {
-    // out = M^p in (M = L or L^H) for `cols` columns, ping-ponging through tmp
+  // out = M^p in (M = L or L^H) for `cols` columns, ping-ponging through tmp.
+  // herm0: column 0 is Hermitian (matrix-free L-QSW: upper-triangle products).
+  void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols,
+            bool herm0 = false) {
+    if (herm0 && box_ok) {
+      const MfOp<double> m = make_mf<double>(*op, adjoint);
+      const unsigned grid = (unsigned)std::min(Nt, 152 * 8);
+      const double2* src = in;
+      for (int k = 0; k < p; ++k) {
+        double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
+        if (adjoint)
+          QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
+        else
+          QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
+        src = dst;
+      }
+      QSW_CUDA_TRY(cudaGetLastError());
+      if (cols > 1) mult(adjoint, p, in + n, out_ + n, tmp ? tmp + n : nullptr, cols - 1);
+      return;
+    }
     const double2* src = in;
     for (int k = 0; k < p; ++k) {
       double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
@@ -590,6 +668,15 @@ struct Estimator {
     return ch;
   }
 
+  // column 1 of a block = column 0 ^dag
+  void mirror_column() {
+    const int tiles = (Nt + 31) / 32;
+    QSW_LAUNCH conj_transpose_kernel<<<(unsigned)std::min<long long>((long long)tiles * tiles, 4096),
+                                       dim3(32, 8), 0, st>>>(Nt, Y.as<double2>(),
+                                                             Y.as<double2>() + (size_t)n);
+    QSW_CUDA_TRY(cudaGetLastError());
+  }
+
   // ones[k n ..] = (A^H)^k 1 for k = 0..p (the all-ones vector and its chain).
   void ensure_ones(int p) {
     const size_t nn = (size_t)n;
@@ -599,18 +686,18 @@ struct Estimator {
       QSW_CUDA_TRY(cudaGetLastError());
       ones_pow = 0;
     }
-    for (; ones_pow < p; ++ones_pow)
+    for (; ones_pow < p; ++ones_pow)   // Hermitian: upper-triangle products
       mult(true, 1, ones.as<double2>() + nn * ones_pow, ones.as<double2>() + nn * (ones_pow + 1),
-           nullptr, 1);
+           nullptr, 1, true);
   }
 
   // Y(:, c) <- (A^H)^p sign(Y(:, c)) = (A^H)^p 1 + (A^H)^p D_c, D_c = sign(Y(:, c)) - 1
-  // supported on the box of the chain that produced Y(:, c).
-  void adjoint_split(int p, Chain* const* src) {
+  // supported on the box of the chain that produced Y(:, c); columns c < cols.
+  void adjoint_split(int p, Chain* const* src, int cols) {
     ensure_ones(p);
     double2* Yp = Y.as<double2>();
     const size_t nn = (size_t)n;
-    for (int c = 0; c < t; ++c) {
+    for (int c = 0; c < cols; ++c) {
       Chain& d = dchain;
       chain_reset(d, true);
       QSW_CUDA_TRY(cudaMemcpyAsync(d.mask.p, src[c]->mask.p, 2 * (size_t)Nt,
@@ -662,7 +749,9 @@ struct Estimator {
     double2* c0 = chain.as<double2>();
     QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, c0);
     QSW_CUDA_TRY(cudaGetLastError());
-    for (int p = 1; p <= pmax; ++p) mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr, t);
+    // column 0 (all ones / n) is Hermitian, and so are its powers
+    for (int p = 1; p <= pmax; ++p)
+      mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr, t, true);
   }
 
   double estimate(int p) {
@@ -675,11 +764,23 @@ struct Estimator {
     int ind_best = 0;
     Chain* ych[2] = {nullptr, nullptr};   // chains behind the columns of Y (k >= 2)
     for (int k = 1;; ++k) {
-      if (k == 1)
+      // L~ maps X^dag to (L~ X)^dag (and so does L~^H): when the two unit vectors
+      // are e_(a,b) and e_(b,a), the second column of Y, and of Z below, is the
+      // first one ^dag.
+      bool mirror = false;
+      if (k == 1) {
         QSW_CUDA_TRY(cudaMemcpyAsync(Yp, chain.as<double2>() + (size_t)n * t * p,
                                      sizeof(double2) * (size_t)n * t, cudaMemcpyDeviceToDevice, st));
-      else   // Y = A^p [e_ind0, e_ind1]
-        for (int c = 0; c < t; ++c) ych[c] = unit_power(ind[c], p, Yp + (size_t)n * c);
+      } else {   // Y = A^p [e_ind0, e_ind1]
+        mirror = t > 1 && ind[1] == (ind[0] / Nt) + Nt * (ind[0] % Nt);
+        ych[0] = unit_power(ind[0], p, Yp);
+        if (mirror) {
+          mirror_column();
+          ych[1] = ych[0];
+        } else {
+          for (int c = 1; c < t; ++c) ych[c] = unit_power(ind[c], p, Yp + (size_t)n * c);
+        }
+      }
       double cn[2] = {0, 0};
       colnorms(Yp, cn);
       const int jbest = (t > 1 && cn[1] > cn[0]) ? 1 : 0;
@@ -692,16 +793,18 @@ struct Estimator {
       est_old = est;
       if (k > kItMax) break;
       // Z = (A^H)^p S, S = sign(Y), in Y
+      const int tz = mirror ? 1 : t;   // columns computed (the mirrored one follows)
       bool split = k >= 2 && split_ok;
-      for (int c = 0; c < t && split; ++c)
+      for (int c = 0; c < tz && split; ++c)
         split = ych[c]->box && !ych[c]->full && ych[c]->box_elems * 16 <= (long long)n;
       if (split) {
-        adjoint_split(p, ych);
+        adjoint_split(p, ych, tz);
       } else {
-        QSW_LAUNCH sign_kernel<<<grid_for((long long)n * t, 256, 4096), 256, 0, st>>>(
-            (long long)n * t, Yp, Xp);
-        mult(true, p, Xp, Yp, Wp, t);
+        QSW_LAUNCH sign_kernel<<<grid_for((long long)n * tz, 256, 4096), 256, 0, st>>>(
+            (long long)n * tz, Yp, Xp);
+        mult(true, p, Xp, Yp, Wp, tz, k == 1);   // k = 1: sign(Y(:, 0)) is Hermitian
       }
+      if (mirror) mirror_column();
       QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
       QSW_CUDA_TRY(cudaGetLastError());
       double hmax, hbest;
