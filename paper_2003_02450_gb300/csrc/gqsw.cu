@@ -209,6 +209,48 @@ gq_pass_b_kernel(GqOp<R> op, const typename V2<R>::T* __restrict__ x,
   }
 }
 
+// Hermitian input (the 1-norm estimator's Hermitian column): pass A forms the
+// W_k and R = x Q^dag over every element, pass B the upper triangle, mirrored,
+// with the diagonal's imaginary part (zero in exact arithmetic) stored as zero.
+template <class R>
+__global__ void __launch_bounds__(kGB)
+gq_pass_ar_kernel(GqOp<R> op, const typename V2<R>::T* __restrict__ x, typename V2<R>::T* w) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int j = blockIdx.x; j < op.Nt; j += gridDim.x)
+    for (int a0 = warp * kItemRows; a0 < op.Nt; a0 += kGW * kItemRows) {
+      int arow[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        const int a = a0 + lane + 32 * u;
+        arow[u] = a < op.Nt ? a : -1;
+      }
+      gq_pass_a<R>(op, x, w, j, arow);
+      gq_pass_a_r<R>(op, x, w, j, arow);
+    }
+}
+
+template <class R>
+__global__ void __launch_bounds__(kGB)
+gq_pass_bh_kernel(GqOp<R> op, const typename V2<R>::T* __restrict__ x,
+                  const typename V2<R>::T* __restrict__ w, typename V2<R>::T* __restrict__ y) {
+  const long long n = (long long)op.Nt * op.Nt;
+  for (long long r = blockIdx.x * (long long)kGB + threadIdx.x; r < n;
+       r += (long long)gridDim.x * kGB) {
+    const int i = (int)(r % op.Nt), j = (int)(r / op.Nt);
+    if (i > j) continue;
+    R yx, yy;
+    gq_element_herm<R>(op, x, w, i, j, yx, yy);
+    typename V2<R>::T v;
+    v.x = yx;
+    v.y = i == j ? (R)0 : yy;
+    y[r] = v;
+    if (i != j) {
+      v.y = -yy;
+      y[j + (long long)op.Nt * i] = v;
+    }
+  }
+}
+
 // ||L~||_1 for one sandwich operator without diagonal entries: column (a, b) of
 // L~ is L~(|a><b|) = Q|a><b| + |a><b|Q^dag + L'|a><b|L'^dag + ports; its entries
 // sit at (i, b), (a, j) and (i, j) with i, j != a, b except the shared (a, b)
@@ -370,6 +412,21 @@ void gq_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y
       QSW_LAUNCH gq_pass_a_kernel<double><<<grid_a, kGB, 0, st>>>(g, xc, west.as<double2>());
     QSW_LAUNCH gq_pass_b_kernel<double><<<grid_b, kGB, 0, st>>>(g, xc, west.as<double2>(), yc, scale);
   }
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
+void gq_apply_herm64(const Op& op, bool adjoint, const double* x, double* y) {
+  cudaStream_t st = op.ctx->stream;
+  const GqOp<double> g = make_gq<double>(op, adjoint);
+  const long long n = op.n;
+  DevBuf& west = const_cast<Op&>(op).gq.west;
+  west.alloc(sizeof(double2) * (size_t)(g.nl + 1) * (size_t)n);
+  const unsigned grid_a = (unsigned)std::min(op.Nt, 152 * 8);
+  const unsigned grid_b = grid_for(n, kGB, 152 * 16);
+  QSW_LAUNCH gq_pass_ar_kernel<double><<<grid_a, kGB, 0, st>>>(
+      g, reinterpret_cast<const double2*>(x), west.as<double2>());
+  QSW_LAUNCH gq_pass_bh_kernel<double><<<grid_b, kGB, 0, st>>>(
+      g, reinterpret_cast<const double2*>(x), west.as<double2>(), reinterpret_cast<double2*>(y));
   QSW_CUDA_TRY(cudaGetLastError());
 }
 

@@ -544,19 +544,24 @@ struct Estimator {
   void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
 
   // out = M^p in (M = L or L^H) for `cols` columns, ping-ponging through tmp.
-  // herm0: column 0 is Hermitian (matrix-free L-QSW: upper-triangle products).
+  // herm0: column 0 is Hermitian (matrix-free operators: upper-triangle products).
   void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols,
             bool herm0 = false) {
-    if (herm0 && box_ok) {
-      const MfOp<double> m = make_mf<double>(*op, adjoint);
+    if (herm0 && (box_ok || op->gq.active)) {
       const unsigned grid = (unsigned)std::min(Nt, 152 * 8);
       const double2* src = in;
       for (int k = 0; k < p; ++k) {
         double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
-        if (adjoint)
-          QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
-        else
-          QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
+        if (op->gq.active) {
+          gq_apply_herm64(*op, adjoint, reinterpret_cast<const double*>(src),
+                          reinterpret_cast<double*>(dst));
+        } else {
+          const MfOp<double> m = make_mf<double>(*op, adjoint);
+          if (adjoint)
+            QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
+          else
+            QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
+        }
         src = dst;
       }
       QSW_CUDA_TRY(cudaGetLastError());

@@ -126,6 +126,7 @@ void build_global(Op& op);                        // device form for op.omega
 template <class R> struct GqOp;
 template <class R> GqOp<R> make_gq(const Op& op, bool adjoint);
 void gq_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
+void gq_apply_herm64(const Op& op, bool adjoint, const double* x, double* y);   // Hermitian x
 bool global_exact_norm(const Op& op, double* one);
 void nm_construct(int N, const int* rowptr, const int* col, const double* w, std::vector<int>& off,
                   ZMat& Hd, ZMat& Ld, ZMat& Hrot);

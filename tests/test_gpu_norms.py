@@ -103,3 +103,49 @@ def test_norm_series_is_an_estimator_outcome(ctx, kind, omega, sources, sinks, o
         assert near <= 1e-10 * exact, (p, est, exact)
     again = LQSW(g, omega, sources=sources, sinks=sinks, ctx=ctx, operator=operator)
     assert np.array_equal(np.asarray(again.norms), got)
+
+
+GLOBAL_CASES = [
+    # (kind, omega, sources, sinks)
+    ("gqsw", 0.5, [(0, 0.6)], [(19, 0.9)]),
+    ("gqsw", 0.0, [], []),
+    ("nm", 0.3, [], []),
+    ("nm", 1.0, [], []),
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _global_exact(kind, omega, sources, sinks):
+    from oracle import gqsw, nm
+    g = W.random_digraph(20, 0.15, 20) if kind == "gqsw" else W.random_digraph(9, 0.3, 9)
+    if kind == "gqsw":
+        walk = gqsw.global_walk(g.dense(), sources=sources, sinks=sinks)
+    else:
+        walk, _ = nm.nm_walk(g.dense())
+    return g, _achievable(gqsw.superoperator(walk, omega))
+
+
+@pytest.mark.parametrize("kind,omega,sources,sinks", GLOBAL_CASES)
+def test_global_walk_norm_series_is_an_estimator_outcome(ctx, kind, omega, sources, sinks):
+    """Global walks take the Hermitian column through the two-pass Hermitian
+    apply (W_k and R = x Q^dag, then the upper triangle, mirrored)."""
+    from paper_2003_02450_gb300 import qsw as C
+    g, vals = _global_exact(kind, omega, tuple(sources), tuple(sinks))
+    build = (lambda: C.qsw_build_gqsw(ctx.handle, g, None, omega, sources, sinks)) \
+        if kind == "gqsw" else (lambda: C.qsw_build_nm_gqsw(ctx.handle, g, omega))
+    op = build()
+    got = np.asarray(C.qsw_op_info(ctx.handle, op)["norms"])
+    C.qsw_op_destroy(op)
+    assert got[0] <= vals[1][0] * (1 + 1e-12) and got[0] >= vals[1][0] / 10
+    for p in range(2, 10):
+        exact, v = vals[p]
+        est = got[p - 1]
+        assert est <= exact * (1 + 1e-12)
+        assert est >= exact / 10
+        k = np.searchsorted(v, est)
+        near = min(abs(v[max(k - 1, 0)] - est), abs(v[min(k, v.size - 1)] - est))
+        assert near <= 1e-10 * exact, (p, est, exact)
+    op = build()
+    again = np.asarray(C.qsw_op_info(ctx.handle, op)["norms"])
+    C.qsw_op_destroy(op)
+    assert np.array_equal(again, got)
