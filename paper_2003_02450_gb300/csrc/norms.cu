@@ -52,6 +52,16 @@ constexpr int kMaxExcl = 16;
 
 __device__ __forceinline__ double cabs(double2 z) { return hypot(z.x, z.y); }
 
+// |z| for the estimator's vector passes: sqrt(x^2 + y^2) where the sum of
+// squares neither overflows nor underflows, hypot otherwise.  On this FP64-lean
+// part hypot's scaling costs several times the issue slots of the plain form,
+// and these passes run over every element of every block the estimator forms.
+__device__ __forceinline__ double cabs_fast(double2 z) {
+  const double s = fma(z.x, z.x, z.y * z.y);
+  if (s < 1e300 && (s > 1e-300 || (z.x == 0.0 && z.y == 0.0))) return sqrt(s);
+  return hypot(z.x, z.y);
+}
+
 __device__ __forceinline__ unsigned long long splitmix64(unsigned long long seed,
                                                          unsigned long long i) {
   unsigned long long z = seed + (i + 1ULL) * 0x9E3779B97F4A7C15ULL;
@@ -106,8 +116,8 @@ __global__ void colabs_partial_kernel(int n, int t, const double2* __restrict__ 
   double a0 = 0, a1 = 0;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    a0 += cabs(Y[r]);
-    if (t > 1) a1 += cabs(Y[n + r]);
+    a0 += cabs_fast(Y[r]);
+    if (t > 1) a1 += cabs_fast(Y[n + r]);
   }
   s0[threadIdx.x] = a0;
   s1[threadIdx.x] = a1;
@@ -151,16 +161,21 @@ __global__ void sign_kernel(long long m, const double2* __restrict__ Y, double2*
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
        e += (long long)gridDim.x * blockDim.x) {
     const double2 y = Y[e];
-    const double a = cabs(y);
-    S[e] = a == 0.0 ? make_double2(1.0, 0.0) : make_double2(y.x / a, y.y / a);
+    const double a = cabs_fast(y);
+    if (a == 0.0) {
+      S[e] = make_double2(1.0, 0.0);
+    } else {
+      const double r = 1.0 / a;
+      S[e] = make_double2(y.x * r, y.y * r);
+    }
   }
 }
 
 __global__ void rowmax_kernel(int n, int t, const double2* __restrict__ Z, double* __restrict__ h) {
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    double v = cabs(Z[r]);
-    if (t > 1) v = fmax(v, cabs(Z[n + r]));
+    double v = cabs_fast(Z[r]);
+    if (t > 1) v = fmax(v, cabs_fast(Z[n + r]));
     h[r] = v;
   }
 }
@@ -463,8 +478,13 @@ __global__ void sign_minus_one_kernel(int Nt, const int* __restrict__ list,
        e += (long long)gridDim.x * blockDim.x) {
     const long long k = list[e % nI] + (long long)Nt * list[Nt + e / nI];
     const double2 y = Y[k];
-    const double a = cabs(y);
-    D[k] = a == 0.0 ? make_double2(0.0, 0.0) : make_double2(y.x / a - 1.0, y.y / a);
+    const double a = cabs_fast(y);
+    if (a == 0.0) {
+      D[k] = make_double2(0.0, 0.0);
+    } else {
+      const double r = 1.0 / a;
+      D[k] = make_double2(y.x * r - 1.0, y.y * r);
+    }
   }
 }
 
