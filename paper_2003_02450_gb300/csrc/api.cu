@@ -248,6 +248,8 @@ qsw_status qsw_create(qsw_ctx** out, int device, void* stream) {
 
 void qsw_destroy(qsw_ctx* ctx) {
   if (ctx && ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx && ctx->copy) cudaStreamDestroy(ctx->copy);
+  if (ctx && ctx->count_h) cudaFreeHost(ctx->count_h);
   delete ctx;
 }
 
@@ -636,10 +638,40 @@ qsw_status qsw_expmv_series_host(qsw_op* h, const double* h_rho0, double t0, dou
     if (h_out) out.alloc(sizeof(double2) * op->n * ((size_t)steps + 1));
     if (h_pops) pops.alloc(sizeof(double) * op->Nt * ((size_t)steps + 1));
     QSW_CUDA_TRY(cudaMemcpyAsync(rho0.p, h_rho0, sizeof(double2) * op->n, cudaMemcpyHostToDevice, st));
-    qsw::run_series(*op, rho0.as<double>(), t0, dt, steps, h_out ? out.as<double>() : nullptr,
-                    h_pops ? pops.as<double>() : nullptr, stats);
-    if (h_out)
-      QSW_CUDA_TRY(cudaMemcpyAsync(h_out, out.p, out.bytes, cudaMemcpyDeviceToHost, st));
+    if (h_out) {
+      // outputs are copied to the host on a second stream as the series kernel
+      // finishes them, overlapping the copies with the remaining Taylor blocks
+      qsw_ctx* c = op->ctx;
+      if (!c->copy) QSW_CUDA_TRY(cudaStreamCreateWithFlags(&c->copy, cudaStreamNonBlocking));
+      if (!c->count_h) {
+        QSW_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&c->count_h), sizeof(int),
+                                   cudaHostAllocMapped));
+        QSW_CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->count_d), c->count_h, 0));
+      }
+      *(volatile int*)c->count_h = 0;
+      const size_t vb = sizeof(double2) * (size_t)op->n;
+      int copied = 0;
+      struct Drain {   // the copy stream must be idle before `out` is released
+        cudaStream_t s;
+        ~Drain() { cudaStreamSynchronize(s); }
+      } drain{c->copy};
+      qsw::OutputSink sink{c->count_h, c->count_d, [&](int k) {
+        QSW_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(h_out) + vb * copied,
+                                     static_cast<char*>(out.p) + vb * copied, vb * (k - copied),
+                                     cudaMemcpyDeviceToHost, c->copy));
+        copied = k;
+      }};
+      qsw::run_series(*op, rho0.as<double>(), t0, dt, steps, out.as<double>(),
+                      h_pops ? pops.as<double>() : nullptr, stats, &sink);
+      if (copied < steps + 1)
+        QSW_CUDA_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(h_out) + vb * copied,
+                                     static_cast<char*>(out.p) + vb * copied,
+                                     vb * (steps + 1 - copied), cudaMemcpyDeviceToHost, st));
+      QSW_CUDA_TRY(cudaStreamSynchronize(c->copy));
+    } else {
+      qsw::run_series(*op, rho0.as<double>(), t0, dt, steps, nullptr,
+                      h_pops ? pops.as<double>() : nullptr, stats);
+    }
     if (h_pops)
       QSW_CUDA_TRY(cudaMemcpyAsync(h_pops, pops.p, sizeof(double) * op->Nt * ((size_t)steps + 1),
                                    cudaMemcpyDeviceToHost, st));

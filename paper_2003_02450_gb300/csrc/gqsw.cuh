@@ -112,7 +112,14 @@ __device__ __forceinline__ void gq_pass_a_r(const GqOp<R>& op, const VT* __restr
     }
 }
 
-// Pass B at element (i, j) of a Hermitian x, from the pass-A products.
+// Pass B at element (i, j) of a Hermitian x, from the pass-A products.  The
+// Q terms come from R = x Q^dag alone, which is right only while x is exactly
+// Hermitian: for an anti-Hermitian part A of x this form gives -Q A in place of
+// Q A, and -Q = i H_tot + 1/2 sum L'^dag L' + ... amplifies A like exp(+t ||L'^dag L'||/2).
+// A diagonal element is real in exact arithmetic but the L'_k W_k sum leaves a
+// rounding-level imaginary part, so it is stored as zero here (and the series
+// kernel takes real diagonals from its input), keeping every term exactly
+// Hermitian.
 template <class R, class VT, class LD = LdGlobal>
 __device__ __forceinline__ void gq_element_herm(const GqOp<R>& op, const VT* __restrict__ x,
                                                 const VT* __restrict__ w, int i, int j, R& yx,
@@ -131,8 +138,8 @@ __device__ __forceinline__ void gq_element_herm(const GqOp<R>& op, const VT* __r
       const VT v = LD::ld(x + (long long)op.jcol[e] * (op.Nt + 1));
       const R r = op.jval[e].x;
       ax = fma(r, v.x, ax);
-      ay = fma(r, v.y, ay);
     }
+    ay = 0;
   }
   yx = ax;
   yy = ay;

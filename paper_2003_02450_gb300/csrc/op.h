@@ -2,6 +2,7 @@
 #pragma once
 
 #include <complex>
+#include <functional>
 
 #include "qsw_internal.h"
 
@@ -9,6 +10,9 @@ struct qsw_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;   // owned: the batched small-walk kernel's stream
+  cudaStream_t copy = nullptr;   // owned: device-to-host copies of finished outputs
+  int* count_h = nullptr;        // owned, host-mapped: final-output counter of a series
+  int* count_d = nullptr;        // its device address
   int num_sms = 0;
   std::string last_error;
 };
@@ -136,8 +140,16 @@ void nm_initial_state(const Op& op, const double* d_p, double* d_state);
 void compute_norms(Op& op, const Csr* L, const Csr* LH);   // null: matrix-free
 // series.cu
 void upload_theta(int device);
+// Receiver of caller outputs as they become final: the series kernel stores
+// the count of final outputs in a host-mapped int (h_count / d_count, zero on
+// entry) and run_series calls ready(count) while it waits for the kernel.
+struct OutputSink {
+  int* h_count;
+  int* d_count;
+  std::function<void(int)> ready;
+};
 void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
-                double* d_pops, qsw_series_stats* stats);
+                double* d_pops, qsw_series_stats* stats, const OutputSink* sink = nullptr);
 void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int steps,
                         double* d_out, double* d_pops, qsw_series_stats* stats);
 double probe_wait_limit(qsw_ctx* ctx);   // seconds until the bounded wait gave up

@@ -29,8 +29,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <chrono>
 #include <mutex>
 #include <string>
+#include <thread>
 
 #include "gqsw.cuh"
 #include "matfree.cuh"
@@ -89,6 +91,7 @@ struct SeriesArgs {
   int njobs;
   Ctrl* ctrl;
   double tol;
+  int* progress;         // host-mapped count of final caller outputs, or null
 };
 
 template <class VT> struct Cplx;
@@ -280,6 +283,9 @@ series_kernel(SeriesArgs a) {
         } else {
           z = __ldcg(Z + r);
         }
+        // a global walk's Hermitian form needs exactly Hermitian terms
+        // (gq_element_herm): the input's diagonal is taken as real
+        if (OPK == kOpGlobalHerm && i == j) z.y = 0.0;
       } else {
         z = __ldcg(Z + r);
       }
@@ -532,6 +538,14 @@ series_kernel(SeriesArgs a) {
       }
       // the next block reads its input Z (this block's last output) in full
       if (!grid_barrier(ctrl)) return;
+    }
+
+    // ---- this block's outputs are final (every block is past the barrier
+    // that ended the last term or the mirror pass): tell a host that copies
+    // finished outputs out while the series runs
+    if (a.progress && J.final_outputs && blockIdx.x == 0 && tid == 0) {
+      __threadfence_system();
+      *(volatile int*)a.progress = J.out_index0 + J.d;
     }
 
     // ---- populations of the finished outputs
@@ -790,7 +804,7 @@ double op_bytes(const Op& op) {
 }
 
 void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
-                double* d_pops, qsw_series_stats* stats) {
+                double* d_pops, qsw_series_stats* stats, const OutputSink* sink) {
   cudaStream_t st = op.ctx->stream;
   const int prec = op.precision == QSW_C64_BULK ? 1 : 0;
   const double* theta = theta_table(op.precision);
@@ -857,6 +871,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   a.njobs = info.njobs;
   a.ctrl = op.ctrl.as<Ctrl>();
   a.tol = tolerance(op.precision);
+  a.progress = (sink && d_out) ? sink->d_count : nullptr;
 
   cudaEvent_t ev0, ev1;
   QSW_CUDA_TRY(cudaEventCreate(&ev0));
@@ -869,6 +884,21 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   QSW_CUDA_TRY(cudaEventRecord(ev1, st));
   Ctrl h{};
   QSW_CUDA_TRY(cudaMemcpyAsync(&h, op.ctrl.p, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));
+  if (a.progress) {
+    // hand finished outputs to the sink while the kernel runs; the loop ends
+    // when the kernel has (its grid barriers bound every wait inside it)
+    int seen = 0;
+    for (;;) {
+      const bool done = cudaEventQuery(ev1) != cudaErrorNotReady;
+      const int k = *(volatile int*)sink->h_count;
+      if (k > seen) {
+        sink->ready(k);
+        seen = k;
+      }
+      if (done) break;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, ev0, ev1);

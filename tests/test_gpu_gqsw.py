@@ -196,3 +196,35 @@ def test_bench_config_first_outputs_full_size(ctx):
     C.qsw_expmv_series(ctx.handle, op, _dev(x0), 0.0, 0.1, 2, out, None)
     assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-10
     C.qsw_op_destroy(op)
+
+
+@pytest.mark.parametrize("kind", ["gqsw", "nm"])
+def test_hermitian_form_long_horizon(ctx, kind):
+    """The Hermitian form takes the Q terms from R = x Q^dag, which assumes an
+    exactly Hermitian term; a rounding-level imaginary diagonal would grow like
+    exp(t ||L'^dag L'|| / 2) (seen as 1e-10 at t = 4.8 on this walk before the
+    diagonal was kept real).  Twenty steps of 0.4 against the oracle."""
+    import torch
+    from oracle import nm
+    from paper_2003_02450_gb300 import qsw as C
+    g = W.random_digraph(16, 0.2, 16) if kind == "gqsw" else W.random_digraph(9, 0.3, 9)
+    if kind == "gqsw":
+        op = C.qsw_build_gqsw(ctx.handle, g, None, 0.6)
+        walk = gqsw.global_walk(g.dense())
+    else:
+        op = C.qsw_build_nm_gqsw(ctx.handle, g, 0.6)
+        walk, _ = nm.nm_walk(g.dense())
+    nt = walk.n_tilde
+    L = gqsw.superoperator(walk, 0.6)
+    x0 = W.vec(W.random_density_matrix(nt, 2))
+    ref = expmv.expmv_series(L, x0, 0.0, 0.4, 20)
+    out = torch.empty((21, nt * nt), dtype=torch.complex128, device="cuda:0")
+    st = C.qsw_expmv_series(ctx.handle, op, _dev(x0), 0.0, 0.4, 20, out, None)
+    assert st["hermitian"] == 1
+    got = _host(out)
+    assert np.max(np.abs(got - ref)) <= 1e-10
+    # every output exactly Hermitian
+    for k in (5, 20):
+        R = got[k].reshape(nt, nt, order="F")
+        assert np.array_equal(R, R.conj().T)
+    C.qsw_op_destroy(op)
