@@ -35,6 +35,7 @@
 //     ranking ties them) costs one column, the other being its mirror.
 // The last two change the rounding of some products, not their values.
 #include <math.h>
+#include <stddef.h>
 
 #include <algorithm>
 
@@ -192,15 +193,19 @@ __device__ __forceinline__ bool better(double va, int ia, double vb, int ib) {
   return va > vb || (va == vb && ia < ib);
 }
 
+// argmax over indices not in ex (host list) nor in dex[0 .. ndex - 1] (indices
+// found by an earlier launch, read on the device: no read-back in between).
 __global__ void argmax_partial_kernel(int n, const double* __restrict__ h, Excl ex,
+                                      const int* __restrict__ dex, int ndex,
                                       double* __restrict__ pv, int* __restrict__ pi) {
   __shared__ double sv[kRedBlock];
   __shared__ int si[kRedBlock];
+  const int d0 = ndex > 0 ? dex[0] : -1;
   double bv = 0;
   int bi = -1;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
-    bool skip = false;
+    bool skip = (int)r == d0;
     for (int q = 0; q < ex.n; ++q) skip |= ex.idx[q] == (int)r;
     if (skip) continue;
     const double v = h[r];
@@ -224,9 +229,17 @@ __global__ void argmax_partial_kernel(int n, const double* __restrict__ h, Excl 
   }
 }
 
+// The row ranking one iteration needs, computed without read-backs in between:
+// the largest h (and h at the current best index), the second largest, and the
+// two largest outside the history.
+struct Select {
+  double hmax, hbest;
+  int idx[4];   // argmax, argmax without it, argmax outside hist, next outside hist
+};
+
 __global__ void argmax_final_kernel(int nparts, const double* __restrict__ pv,
                                     const int* __restrict__ pi, const double* __restrict__ h,
-                                    int probe, double* __restrict__ out) {
+                                    int probe, Select* __restrict__ out, int slot) {
   __shared__ double sv[kRedGrid];
   __shared__ int si[kRedGrid];
   for (int b = threadIdx.x; b < kRedGrid; b += blockDim.x) {
@@ -243,9 +256,11 @@ __global__ void argmax_final_kernel(int nparts, const double* __restrict__ pv,
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    out[0] = sv[0];
-    out[1] = (double)si[0];
-    out[2] = probe >= 0 ? h[probe] : 0.0;
+    out->idx[slot] = si[0];
+    if (slot == 0) {
+      out->hmax = sv[0];
+      out->hbest = probe >= 0 ? h[probe] : 0.0;
+    }
   }
 }
 
@@ -537,10 +552,21 @@ struct Chain {
   bool box = false;         // support tracked (matrix-free L-QSW operator)
   bool full = false;        // the box is the whole matrix (known on the host)
   long long box_elems = 0;  // |I| |J| at the last host read
+  int* pending = nullptr;   // pinned words of a box size in flight to the host
   DevBuf v, w, mask, mask2, list, count;
 };
 
 constexpr int kChainsMax = 8;
+
+// Small pinned host array per thread (box sizes in flight to the host), kept
+// for the thread's lifetime; portable across devices.
+int* pinned_words() {
+  static thread_local int* words = nullptr;
+  if (!words)
+    QSW_CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&words), sizeof(int) * 2 * kChainsMax,
+                               cudaHostAllocPortable));
+  return words;
+}
 constexpr size_t kChainBytes = size_t(1) << 30;   // device memory for cached chains
 constexpr size_t kOnesChainBytes = size_t(4) << 30;
 
@@ -551,7 +577,7 @@ struct Estimator {
   const Op* op;
   const Csr* A;    // CSR operator, or null for matrix-free
   const Csr* AH;
-  DevBuf X, Y, W, h, partials, pv, pi, out;
+  DevBuf X, Y, W, h, partials, pv, pi, out, sel;
   bool box_ok = false;      // matrix-free L-QSW: unit chains track their box
   bool split_ok = false;    // ... and the adjoint step may split off (A^H)^p 1
   Chain chains[kChainsMax];
@@ -631,12 +657,24 @@ struct Estimator {
     ++ch.pow;
   }
 
+  // The box size of a chain reaches the host with the next read-back the
+  // iteration makes anyway (a copy into pinned words queued now, settled after
+  // that sync); until then the chain keeps its box products, which are exact
+  // for a full box too.
   void read_box(Chain& ch) {
-    int c[2] = {0, 0};
-    QSW_CUDA_TRY(cudaMemcpyAsync(c, ch.count.p, sizeof(c), cudaMemcpyDeviceToHost, st));
-    sync();
-    ch.box_elems = (long long)c[0] * c[1];
-    ch.full = c[0] == Nt && c[1] == Nt;
+    int* w = pinned_words() + 2 * (&ch - chains);
+    QSW_CUDA_TRY(cudaMemcpyAsync(w, ch.count.p, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    ch.pending = w;
+  }
+
+  void settle() {
+    for (int q = 0; q < n_chains; ++q) {
+      Chain& ch = chains[q];
+      if (!ch.pending) continue;
+      ch.box_elems = (long long)ch.pending[0] * ch.pending[1];
+      ch.full = ch.pending[0] == Nt && ch.pending[1] == Nt;
+      ch.pending = nullptr;
+    }
   }
 
   // Both vectors (and the masks) cleared; the box, when tracked, still empty.
@@ -650,6 +688,7 @@ struct Estimator {
     ch.full = false;
     ch.pow = 0;
     ch.box_elems = 0;
+    ch.pending = nullptr;
     if (with_box) {
       ch.mask.alloc(2 * (size_t)Nt);
       ch.mask2.alloc(2 * (size_t)Nt);
@@ -746,23 +785,36 @@ struct Estimator {
     QSW_LAUNCH sum_partials_kernel<<<1, 256, 0, st>>>(kRedGrid, partials.as<double>(), out.as<double>());
     QSW_CUDA_TRY(cudaMemcpyAsync(host2, out.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     sync();
+    settle();
   }
 
-  // argmax of h over indices not in ex; also returns h[probe]
-  void argmax(const std::vector<int>& ex, int probe, double* best, int* idx, double* hprobe) {
-    Excl e{};
-    e.n = (int)std::min<size_t>(ex.size(), kMaxExcl);
-    for (int q = 0; q < e.n; ++q) e.idx[q] = ex[q];
-    QSW_LAUNCH argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(n, h.as<double>(), e, pv.as<double>(),
-                                                          pi.as<int>());
-    QSW_LAUNCH argmax_final_kernel<<<1, 256, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(), h.as<double>(),
-                                          probe, out.as<double>());
-    double o[3];
-    QSW_CUDA_TRY(cudaMemcpyAsync(o, out.p, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  // The iteration's ranking of h (Select), one read-back: four argmax passes
+  // queued back to back, the later ones excluding earlier results on the device.
+  void select(const std::vector<int>& hist, int probe, Select* res) {
+    Excl none{};
+    Excl eh{};
+    eh.n = (int)std::min<size_t>(hist.size(), kMaxExcl);
+    for (int q = 0; q < eh.n; ++q) eh.idx[q] = hist[q];
+    Select* d = sel.as<Select>();
+    const int* didx = reinterpret_cast<const int*>(reinterpret_cast<const char*>(d) + offsetof(Select, idx));
+    struct Pass {
+      const Excl* ex;
+      const int* dex;
+      int slot;
+    } passes[4] = {{&none, nullptr, 0}, {&none, didx + 0, 1}, {&eh, nullptr, 2}, {&eh, didx + 2, 3}};
+    const int np = t > 1 ? 4 : 1;
+    for (int q = 0; q < np; ++q) {
+      QSW_LAUNCH argmax_partial_kernel<<<kRedGrid, kRedBlock, 0, st>>>(
+          n, h.as<double>(), *passes[q].ex, passes[q].dex, passes[q].dex ? 1 : 0, pv.as<double>(),
+          pi.as<int>());
+      QSW_LAUNCH argmax_final_kernel<<<1, 256, 0, st>>>(kRedGrid, pv.as<double>(), pi.as<int>(),
+                                                        h.as<double>(), q == 0 ? probe : -1, d,
+                                                        passes[q].slot);
+    }
+    QSW_CUDA_TRY(cudaGetLastError());
+    QSW_CUDA_TRY(cudaMemcpyAsync(res, d, sizeof(Select), cudaMemcpyDeviceToHost, st));
     sync();
-    *best = o[0];
-    *idx = (int)o[1];
-    if (hprobe) *hprobe = o[2];
+    settle();
   }
 
   // chain[p-1] = A^p X0 for the common starting block X0, p = 1..pmax: every
@@ -832,26 +884,19 @@ struct Estimator {
       if (mirror) mirror_column();
       QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
       QSW_CUDA_TRY(cudaGetLastError());
-      double hmax, hbest;
-      int imax;
-      argmax({}, ind_best, &hmax, &imax, &hbest);
-      if (k >= 2 && hmax == hbest) break;
+      Select pick;
+      select(hist, ind_best, &pick);
+      if (k >= 2 && pick.hmax == pick.hbest) break;
       int fresh[2] = {-1, -1};
       if (t > 1) {
-        double v2;
-        int i2;
-        argmax({imax}, -1, &v2, &i2, nullptr);
-        const bool in0 = std::find(hist.begin(), hist.end(), imax) != hist.end();
-        const bool in1 = std::find(hist.begin(), hist.end(), i2) != hist.end();
+        const bool in0 = std::find(hist.begin(), hist.end(), pick.idx[0]) != hist.end();
+        const bool in1 = std::find(hist.begin(), hist.end(), pick.idx[1]) != hist.end();
         if (in0 && in1) break;
-        std::vector<int> ex = hist;
-        double fv;
-        argmax(ex, -1, &fv, &fresh[0], nullptr);
-        ex.push_back(fresh[0]);
-        argmax(ex, -1, &fv, &fresh[1], nullptr);
+        fresh[0] = pick.idx[2];
+        fresh[1] = pick.idx[3];
         if (fresh[0] < 0 || fresh[1] < 0) break;   // fewer than t unused unit vectors
       } else {
-        fresh[0] = imax;
+        fresh[0] = pick.idx[0];
       }
       ind[0] = fresh[0];
       ind[1] = fresh[1];
@@ -906,6 +951,7 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.pv.alloc(sizeof(double) * kRedGrid);
   E.pi.alloc(sizeof(int) * kRedGrid);
   E.out.alloc(sizeof(double) * 4);
+  E.sel.alloc(sizeof(Select));
   E.Nt = op.Nt;
   E.box_ok = !L && !op.gq.active;
   E.split_ok = E.box_ok &&
