@@ -11,7 +11,8 @@
 //   the row-norm ranking go to the smaller index.
 //
 // Every product and reduction runs in FP64 on the device; the host only
-// follows the algorithm's branches on the few scalars each iteration returns.
+// follows the algorithm's branches on the few scalars each iteration returns
+// (one read-back for the column norms, one for the row ranking).
 // All reductions use a fixed grid and a fixed summation order, so repeated
 // builds give bit-identical estimates.
 //
