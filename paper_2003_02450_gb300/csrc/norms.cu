@@ -818,18 +818,27 @@ struct Estimator {
     settle();
   }
 
-  // chain[p-1] = A^p X0 for the common starting block X0, p = 1..pmax: every
-  // estimate's first product comes from this one chain of pmax products.
-  DevBuf chain;
-  void make_chain(int pmax) {
+  // A^p X0 for the common starting block X0: every estimate's first product
+  // comes from this one chain.  The estimates run in increasing p, so only the
+  // current power is kept (and advanced in place), not all nine.
+  DevBuf chain, chain_tmp;
+  int chain_pow = -1;
+  void start_chain() {
     const size_t blk = (size_t)n * t;
-    chain.alloc(sizeof(double2) * blk * (pmax + 1));
-    double2* c0 = chain.as<double2>();
-    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, c0);
+    chain.alloc(sizeof(double2) * blk);
+    chain_tmp.alloc(sizeof(double2) * blk);
+    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, chain.as<double2>());
     QSW_CUDA_TRY(cudaGetLastError());
+    chain_pow = 0;
+  }
+  const double2* chain_power(int p) {
+    QSW_CHECK_ARG(chain_pow >= 0 && chain_pow <= p, QSW_ERR_CUDA, "estimator chain out of order");
     // column 0 (all ones / n) is Hermitian, and so are its powers
-    for (int p = 1; p <= pmax; ++p)
-      mult(false, 1, c0 + blk * (p - 1), c0 + blk * p, nullptr, t, true);
+    for (; chain_pow < p; ++chain_pow) {
+      mult(false, 1, chain.as<double2>(), chain_tmp.as<double2>(), nullptr, t, true);
+      std::swap(chain, chain_tmp);
+    }
+    return chain.as<double2>();
   }
 
   double estimate(int p) {
@@ -847,8 +856,8 @@ struct Estimator {
       // first one ^dag.
       bool mirror = false;
       if (k == 1) {
-        QSW_CUDA_TRY(cudaMemcpyAsync(Yp, chain.as<double2>() + (size_t)n * t * p,
-                                     sizeof(double2) * (size_t)n * t, cudaMemcpyDeviceToDevice, st));
+        QSW_CUDA_TRY(cudaMemcpyAsync(Yp, chain_power(p), sizeof(double2) * (size_t)n * t,
+                                     cudaMemcpyDeviceToDevice, st));
       } else {   // Y = A^p [e_ind0, e_ind1]
         mirror = t > 1 && ind[1] == (ind[0] / Nt) + Nt * (ind[0] % Nt);
         ych[0] = unit_power(ind[0], p, Yp);
@@ -960,10 +969,10 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.n_chains = (int)std::min<size_t>(
       kChainsMax, std::max<size_t>(2, kChainBytes / (2 * sizeof(double2) * (size_t)n)));
   if (one_estimated) {   // several sandwich operators (or diagonal entries): estimate p = 1 too
-    E.make_chain(kNormPowers);
+    E.start_chain();
     one = E.estimate(1);
   } else if (one != 0.0) {
-    E.make_chain(kNormPowers);
+    E.start_chain();
   }
   op.norms[0] = one;
   for (int p = 2; p <= kNormPowers; ++p) op.norms[p - 1] = one == 0.0 ? 0.0 : E.estimate(p);
