@@ -30,6 +30,9 @@
  *   caller; "h_" arguments are host pointers.  Every call is ordered on the
  *   context's CUDA stream; calls that return results or statistics to the host
  *   synchronise that stream before returning.
+ * - A context, and the operators built on it, serve one host thread at a
+ *   time; separate contexts (each with its own stream) may run concurrently.
+ *   The qsw_server_* calls are safe from any thread.
  * - No exception crosses this boundary: every call returns a qsw_status and,
  *   on failure, a message retrievable with qsw_last_error().  Failed calls
  *   leave caller buffers in an unspecified state and leak nothing.
@@ -267,7 +270,13 @@ qsw_status qsw_expmv_series_noalloc(qsw_op* op, const double* d_rho0, double t0,
 
 /* Same computation with HOST buffers: h_rho0 (n complex128), h_out / h_pops
  * as d_out / d_pops above but in host memory (pinned memory is fastest).  The
- * host<->device copies are part of the call. */
+ * host<->device copies are part of the call: outputs are copied to h_out on a
+ * second stream owned by the context as soon as the Taylor block that computes
+ * them has finished (the series kernel reports its progress through a
+ * host-mapped counter owned by the context), overlapping the copies with the
+ * later blocks; populations are copied after the kernel.  Results are the
+ * same bits as qsw_expmv_series with device buffers.  One call at a time per
+ * context. */
 qsw_status qsw_expmv_series_host(qsw_op* op, const double* h_rho0, double t0, double dt,
                                  int32_t steps, double* h_out, double* h_pops,
                                  qsw_series_stats* stats);
