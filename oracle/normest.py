@@ -17,8 +17,12 @@ The paper precomputes the series {||L~^p||_1, p = 1..9} when a walk is built
 
 Pinned by tests/test_oracle_norms.py: exact powers against dense numpy powers,
 est <= exact always, est == exact on matrices where the estimator provably
-hits the maximising column, and SplitMix64 against its published reference
-outputs.
+hits the maximising column, SplitMix64 against its published reference
+outputs, and iteration traces derived by hand for 3 x 3 complex matrices (the
+column norms, row maxima, chosen unit vectors and stop reason of every
+iteration): cases where A^T in place of A^H, or a real-valued sign, changes the
+chosen columns and the estimate, a history that leaves no fresh unit vector
+(estimate 3 where ||A||_1 = 2 + sqrt 2), and the iteration cap.
 """
 from __future__ import annotations
 
@@ -71,8 +75,15 @@ def _apply_power(A, X, p):
     return X
 
 
-def onenorm_power_est(A, p: int, t: int = 2, itmax: int = 5, seed: int = NORMEST_SEED) -> float:
-    """Higham--Tisseur Algorithm 2.4 estimate of ||A^p||_1 (a lower bound)."""
+def onenorm_power_est(A, p: int, t: int = 2, itmax: int = 5, seed: int = NORMEST_SEED,
+                      trace: list | None = None) -> float:
+    """Higham--Tisseur Algorithm 2.4 estimate of ||A^p||_1 (a lower bound).
+
+    ``trace``, when given, receives one dict per iteration k: the column
+    1-norms of Y = A^p X, the unit-vector indices X was made of (None at k = 1),
+    the row maxima h of Z = (A^H)^p sign(Y) when they were formed, the indices
+    chosen for the next iteration, and the reason the loop ended ("est <= est_old",
+    "itmax", "h max at ind_best", "ind in history", "no fresh index")."""
     A = sp.csr_matrix(A, dtype=np.complex128)
     AH = sp.csr_matrix(A.conj().T)
     n = A.shape[0]
@@ -94,25 +105,33 @@ def onenorm_power_est(A, p: int, t: int = 2, itmax: int = 5, seed: int = NORMEST
     while True:
         Y = _apply_power(A, X, p)
         colnorms = np.sum(np.abs(Y), axis=0)
+        rec = {"k": k, "colnorms": colnorms.copy(), "from": None if k == 1 else ind.tolist()}
+        if trace is not None:
+            trace.append(rec)
         jbest = int(np.argmax(colnorms))
         est = float(colnorms[jbest])
         if est > est_old or k == 2:
             ind_best = int(ind[jbest])
         if k >= 2 and est <= est_old:
             est = est_old
+            rec["stop"] = "est <= est_old"
             break
         est_old = est
         if k > itmax:
+            rec["stop"] = "itmax"
             break
         absY = np.abs(Y)
         S = np.where(absY == 0, 1.0 + 0j, Y / np.where(absY == 0, 1.0, absY))
         Z = _apply_power(AH, S, p)
         h = np.max(np.abs(Z), axis=1)
+        rec["h"] = h.copy()
         if k >= 2 and np.max(h) == h[ind_best]:
+            rec["stop"] = "h max at ind_best"
             break
         order = np.argsort(-h, kind="stable")   # h descending, ties by index
         if t > 1:
             if set(order[:t].tolist()) <= set(ind_hist):
+                rec["stop"] = "ind in history"
                 break
             fresh = []
             for i in order:             # first t indices of the sorted order not yet used
@@ -121,10 +140,12 @@ def onenorm_power_est(A, p: int, t: int = 2, itmax: int = 5, seed: int = NORMEST
                     if len(fresh) == t:
                         break
             if len(fresh) < t:      # fewer than t unused unit vectors remain
+                rec["stop"] = "no fresh index"
                 break
             ind = np.array(fresh, dtype=np.int64)
         else:
             ind = order[:t].astype(np.int64)
+        rec["next"] = ind.tolist()
         X = np.zeros((n, t), dtype=np.complex128)
         for c, i in enumerate(ind):
             X[i, c] = 1.0
