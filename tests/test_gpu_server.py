@@ -73,7 +73,7 @@ def test_server_mix_matches_oracle_and_alone():
     # alone: the same request through a fresh server, one at a time
     srv = C.qsw_server_create(0, workers=1, max_batch=1)
     try:
-        for r in reqs[:6]:
+        for r in reqs:
             g, omega, rho0, t0, steps, prec = r.meta
             alone = C.Request(g, omega, t0, 0.1, steps, prec, rho0=rho0)
             C.qsw_server_submit(srv, alone)
@@ -136,3 +136,80 @@ def test_server_concurrent_small_batches_of_mixed_sizes():
         ref = _oracle_pops(g, omega, rho0, t0, r.c.steps)
         tol = 1e-10 if prec == "c128" else 1e-4
         assert np.max(np.abs(r.pops - ref)) <= tol
+
+
+def _big_requests(seed):
+    """Config-5-style walks that take the whole-GPU series kernel (N >= 160):
+    directed Erdos-Renyi graphs of mean out-degree 8, w ~ U(0.5, 1.5), each
+    graph served once in complex128 and once in complex64 bulk."""
+    from paper_2003_02450_gb300 import qsw as C
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for k, n in enumerate((160, 300, 600)):
+        g = W.erdos_renyi_mean_degree(n, 8.0, seed * 100 + k)
+        omega = float(rng.uniform(0, 1))
+        steps = int(rng.integers(5, 25))
+        rho0 = W.random_pure_states(n, 1, seed * 100 + k)[0] if k % 2 else W.basis_state(n, 0)
+        for prec in ("c128", "c64"):
+            if k % 2:
+                r = C.Request(g, omega, 0.0, 0.1, steps, prec, rho0=rho0)
+            else:
+                r = C.Request(g, omega, 0.0, 0.1, steps, prec, populations=np.eye(n)[0])
+            r.meta = (g, omega, rho0, 0.0, steps, prec)
+            r.key = k
+            reqs.append(r)
+    return reqs
+
+
+def test_server_mix_with_whole_gpu_walks_matches_oracle_and_alone():
+    """Whole-GPU walks (cooperative series kernel on one worker's stream) run
+    beside batched small walks on the other workers' streams.  Every result
+    matches the oracle and is bit-identical to the same request served alone."""
+    ensure_built()
+    from paper_2003_02450_gb300 import qsw as C
+    small = _requests(18, 21)
+    big = _big_requests(31)
+    mix = []
+    for k in range(max(len(small), len(big))):   # interleave: big ones arrive among small ones
+        if k < len(big):
+            mix.append(big[k])
+        if k < len(small):
+            mix.append(small[k])
+    srv = C.qsw_server_create(0, workers=3, max_batch=6, memory_budget_bytes=4e9)
+    try:
+        def submit(part):
+            for r in part:
+                C.qsw_server_submit(srv, r)
+                time.sleep(0.003)
+        ths = [threading.Thread(target=submit, args=(mix[i::3],)) for i in range(3)]
+        for t in ths:
+            t.start()
+        for t in ths:
+            t.join()
+        for r in mix:
+            C.qsw_server_wait(srv, r, 600.0)
+        st = C.qsw_server_stats(srv)
+    finally:
+        C.qsw_server_destroy(srv)
+    assert st["queued"] == 0 and st["batches"] >= 4
+    # oracle: one FP64 series per distinct walk (the c128 / c64 pair of a big graph share it)
+    refs = {}
+    for r in mix:
+        g, omega, rho0, t0, steps, prec = r.meta
+        key = ("big", r.key) if hasattr(r, "key") else ("small", id(r))
+        if key not in refs:
+            refs[key] = _oracle_pops(g, omega, rho0, t0, steps)
+        tol = 1e-10 if prec == "c128" else 1e-4
+        err = np.max(np.abs(r.pops - refs[key]))
+        assert err <= tol, (g.n, prec, err)
+    # alone: each request through a fresh one-worker server, one at a time
+    srv = C.qsw_server_create(0, workers=1, max_batch=1)
+    try:
+        for r in mix:
+            g, omega, rho0, t0, steps, prec = r.meta
+            alone = C.Request(g, omega, t0, 0.1, steps, prec, rho0=rho0)
+            C.qsw_server_submit(srv, alone)
+            C.qsw_server_wait(srv, alone, 600.0)
+            assert np.array_equal(alone.pops, r.pops), (g.n, prec)
+    finally:
+        C.qsw_server_destroy(srv)
