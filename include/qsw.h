@@ -226,6 +226,11 @@ qsw_status qsw_apply(const qsw_op* op, const double* d_x, double* d_y);
  *   d_pops : (steps+1) x N~ doubles (device), p_i(t_k) = Re rho_ii(t_k), or NULL.
  *   stats  : host struct or NULL.
  * At least one of d_out / d_pops must be non-NULL.  Synchronises the stream.
+ * Any number of output times: an Algorithm 5.2 block of d > 128 outputs runs
+ * as ceil(d / 128) jobs that each start from the block's input and form its
+ * Taylor powers again (each output gets exactly the arithmetic of the whole
+ * block; the extra cost is the repeated operator applications).  With d_out
+ * NULL the outputs of one block are kept in a device ring of d + 1 states.
  * Errors: INVALID_ARG, OOM, NOT_CONVERGED (a device wait exceeded its limit),
  * CUDA. */
 qsw_status qsw_expmv_series(qsw_op* op, const double* d_rho0, double t0, double dt,
@@ -260,7 +265,9 @@ qsw_status qsw_expmv_series(qsw_op* op, const double* d_rho0, double t0, double 
  *   words and the Hermiticity-check accumulators).
  * - The first call on a device looks up the array's device address
  *   (cudaGetSymbolAddress, checked; CUDA error otherwise); make that first
- *   call before any stream capture.
+ *   call before any stream capture.  The address is kept for the life of
+ *   the process, so the device's primary context must live as long: do not
+ *   call cudaDeviceReset between calls.
  * - Every call on a device shares the array: calls in flight at the same time
  *   on one device (other threads, contexts or streams) race.
  * - stats->kernel_ms is 0 (no timing events are created). */
@@ -311,8 +318,9 @@ typedef struct {
  * [(k n0 + c) N~_w + i]).  Each walk is handled by one cluster of thread
  * blocks; walks with Hermitian right-hand sides are computed on upper
  * triangles.  The 1-norm estimates are computed on the device only when Code
- * Fragment 3.1 needs them for the walk's time span.  At most 64 output times
- * per Taylor block.  Synchronises the stream.
+ * Fragment 3.1 needs them for the walk's time span.  Any number of output
+ * times: Taylor blocks of more than 64 outputs run as several jobs from the
+ * block's input, as in qsw_expmv_series.  Synchronises the stream.
  * Errors: INVALID_ARG, OOM, CUDA. */
 qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,
@@ -471,6 +479,11 @@ void qsw_server_destroy(qsw_server* server);
 /* Number of CUDA kernels this library has launched in the calling process
  * (all contexts), for launch accounting.  Pure host call. */
 int64_t qsw_kernel_launches(void);
+
+/* Number of device-memory allocations (stream-ordered cudaMallocAsync) the
+ * library has made in the calling process, all contexts.  Pure host call; a
+ * caller can read it around a call to see whether that call allocated. */
+int64_t qsw_device_allocations(void);
 
 /* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
  * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor

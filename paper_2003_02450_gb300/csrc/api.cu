@@ -16,6 +16,7 @@ using qsw::Error;
 using qsw::Op;
 
 std::atomic<long long> qsw::g_launches{0};
+std::atomic<long long> qsw::g_device_allocs{0};
 
 namespace {
 
@@ -691,6 +692,8 @@ qsw_status qsw_populations(const qsw_op* h, const double* d_rho, int32_t count, 
 }
 
 int64_t qsw_kernel_launches(void) { return qsw::g_launches.load(); }
+
+int64_t qsw_device_allocations(void) { return qsw::g_device_allocs.load(); }
 
 qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,

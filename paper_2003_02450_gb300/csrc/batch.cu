@@ -57,7 +57,8 @@ constexpr int kBW = kBT / 32;
 constexpr int kMaxRhs = 4;
 constexpr int kItMax = 5;
 constexpr int kMaxHist = 2 * (kItMax + 1);
-constexpr int kBDMax = 64;    // outputs per Taylor block in the batched kernel
+constexpr int kBDMax = 64;    // outputs per Taylor job in the batched kernel (larger
+                              // blocks are split into jobs that recompute the powers)
 constexpr unsigned long long kSeed = 0x51535700ULL;
 
 struct BWalk {
@@ -589,7 +590,7 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
     for (int k = threadIdx.x; k < J.d; k += kBT) {
       s_c1[k] = znorm;
       s_coef[k] = 1.0;
-      s_step[k] = (double)(k + 1) / J.d;
+      s_step[k] = (double)(J.k_off + k + 1) / J.d_block;
       s_active[k] = 1;
       s_extra[k] = 0ULL;
     }
@@ -810,8 +811,8 @@ batch_series_kernel(BArgs a) {
     // plan on the device from the walk's own norms
     if (cl.block_rank() == 0 && threadIdx.x == 0) {
       const PlanInfo info = plan_series(W.dp, c_theta_b[W.f32 ? 1 : 0], W.t0, W.dt, W.steps, W.n0,
-                                        W.ring, W.jobs, W.njobs);
-      if (info.njobs != W.njobs || info.max_d > kBDMax) W.counters[2] = 1;
+                                        W.ring, W.jobs, W.njobs, kBDMax);
+      if (info.njobs != W.njobs || info.max_job_d > kBDMax) W.counters[2] = 1;
     }
     cl.sync();
     if (__ldcg(&W.counters[2])) continue;   // L2 read: every CTA sees rank 0's flag
@@ -844,8 +845,8 @@ __global__ void __launch_bounds__(kBT) batch_small_kernel(BArgs a) {
     BWalk& W = a.walks[wi];
     if (threadIdx.x == 0) {
       const PlanInfo info = plan_series(W.dp, c_theta_b[W.f32 ? 1 : 0], W.t0, W.dt, W.steps, W.n0,
-                                        W.ring, W.jobs, W.njobs);
-      if (info.njobs != W.njobs || info.max_d > kBDMax) W.counters[2] = 1;
+                                        W.ring, W.jobs, W.njobs, kBDMax);
+      if (info.njobs != W.njobs || info.max_job_d > kBDMax) W.counters[2] = 1;
     }
     __syncthreads();
     if (*((volatile long long*)&W.counters[2])) continue;
@@ -996,9 +997,7 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     BWalk& W = hw[w];
     const double* theta = theta_table(W.f32 ? QSW_C64_BULK : QSW_C128);
     const PlanInfo info = plan_series(&dps[(kNormPowers + 1) * w], theta, W.t0, W.dt, W.steps,
-                                      n0, 0, nullptr, 0);
-    QSW_CHECK_ARG(info.max_d <= kBDMax, QSW_ERR_INVALID_ARG,
-                  "batched series: more than 64 outputs per Taylor block");
+                                      n0, 0, nullptr, 0, kBDMax);
     W.njobs = info.njobs;
     W.ring = info.max_d + 1;
     const size_t vb = W.f32 ? sizeof(float2) : sizeof(double2);

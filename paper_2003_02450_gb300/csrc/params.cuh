@@ -60,22 +60,30 @@ __host__ __device__ inline Params select_params(const double* dp, const double* 
 // kernel maps them to memory with the same rule.
 __host__ __device__ inline PlanInfo plan_series(const double* dp, const double* theta, double t0,
                                                 double dt, int steps, int n0, int ring, Job* jobs,
-                                                int max_jobs) {
+                                                int max_jobs, int dmax) {
   PlanInfo info{};
   int nj = 0;
+  // one block of d outputs sharing Z, as ceil(d / dmax) jobs
   auto push = [&](int z, int out0, int d, int m, int fin, double hspan) {
-    if (jobs && nj < max_jobs) {
-      Job& j = jobs[nj];
-      j.z_slot = z;
-      j.out_slot0 = out0;
-      j.out_index0 = out0;
-      j.d = d;
-      j.m = m;
-      j.final_outputs = fin;
-      j.hspan = hspan;
-    }
-    ++nj;
     if (d > info.max_d) info.max_d = d;
+    for (int k0 = 0; k0 < d; k0 += dmax) {
+      const int dc = d - k0 < dmax ? d - k0 : dmax;
+      if (jobs && nj < max_jobs) {
+        Job& j = jobs[nj];
+        j.z_slot = z;
+        j.out_slot0 = out0 + k0;
+        j.out_index0 = out0 + k0;
+        j.d = dc;
+        j.m = m;
+        j.final_outputs = fin;
+        j.k_off = k0;
+        j.d_block = d;
+        j.hspan = hspan;
+      }
+      ++nj;
+      info.outputs += dc;
+      if (dc > info.max_job_d) info.max_job_d = dc;
+    }
   };
   (void)ring;
   // State 0: Algorithm 3.2 for t0 A with its own parameters; stage i feeds

@@ -21,6 +21,9 @@ constexpr int kMaxGlobalOps = 8;   // Lindblad operators of a global-interaction
 
 // Number of kernels this library has launched in this process (all devices).
 extern std::atomic<long long> g_launches;
+// Number of device allocations (DevBuf::alloc, the library's only device
+// allocator) made in this process.
+extern std::atomic<long long> g_device_allocs;
 #define QSW_LAUNCH ::qsw::g_launches.fetch_add(1, std::memory_order_relaxed),
 
 // ------------------------------------------------------------------ errors
@@ -84,6 +87,7 @@ struct DevBuf {
     release();
     if (nbytes == 0) return;
     s = current_stream();
+    g_device_allocs.fetch_add(1, std::memory_order_relaxed);
     QSW_CUDA_TRY(cudaMallocAsync(&p, nbytes, s));
     bytes = nbytes;
   }
@@ -106,31 +110,40 @@ struct Params {
 // Identical code on host and device (IEEE operations only: *, /, ceil, <=).
 __host__ __device__ Params select_params(const double* dp, const double* theta, double t, int n0);
 
-// One Taylor block of the device program: outputs F_k = sum_p (k/d)^p Khat_p,
-// k = 1..d, with Khat_p = (hspan/p) L Khat_{p-1}, Khat_0 = Z.
+// One Taylor job of the device program: outputs k = k_off + 1 .. k_off + d of
+// a block of d_block outputs, F_k = sum_p (k/d_block)^p Khat_p, with
+// Khat_p = (hspan/p) L Khat_{p-1}, Khat_0 = Z.  A block with more outputs than
+// a kernel keeps state for is split into chunks (k_off > 0 for all but the
+// first): every chunk starts again from the block's Z and forms the same
+// powers, so each output gets exactly the arithmetic of the unsplit block.
 struct Job {
   int z_slot;        // slot of Z (-1: the caller's rho0)
-  int out_slot0;     // slot of F_1; F_k in slot out_slot0 + k - 1 (mod ring)
-  int out_index0;    // series index of F_1 (for populations), or -1
-  int d;             // outputs in this block
+  int out_slot0;     // slot of this job's first output; the rest follow (mod ring)
+  int out_index0;    // series index of this job's first output (for populations), or -1
+  int d;             // outputs in this job
   int m;             // m* (max Taylor degree)
-  int final_outputs; // 1 if F_k are final series states (write populations)
-  double hspan;      // d * h: Khat_p = (hspan/p) L Khat_{p-1}
+  int final_outputs; // 1 if the outputs are final series states (write populations)
+  int k_off;         // outputs of the block before this job
+  int d_block;       // outputs of the whole block (coefficient (k / d_block)^p)
+  double hspan;      // d_block * h: Khat_p = (hspan/p) L Khat_{p-1}
 };
 
 // Whole-series plan (Algorithm 5.2, with Algorithm 3.2 for the first state
 // and for the stepwise branch).  Built identically on host and device.
 struct PlanInfo {
   int njobs;
-  int max_d;
+  int max_d;       // largest block (outputs sharing one Z): sizes an output ring
+  int max_job_d;   // largest job (<= the chunk limit)
+  int outputs;     // sum of the jobs' outputs (each initialised once from its Z)
   int m0, s0, m_star, s, step_m, step_s, d;
 };
 
 // Writes up to max_jobs jobs (jobs may be null to only count).  `ring` > 0
 // maps series index k to slot k % ring (workspace ring); ring == 0 maps index
-// k to slot k (caller's output array).
+// k to slot k (caller's output array).  Blocks of more than `dmax` outputs are
+// split into ceil(d / dmax) jobs.
 __host__ __device__ PlanInfo plan_series(const double* dp, const double* theta, double t0,
                                          double dt, int steps, int n0, int ring, Job* jobs,
-                                         int max_jobs);
+                                         int max_jobs, int dmax);
 
 }  // namespace qsw

@@ -47,7 +47,8 @@ namespace {
 
 constexpr int kBlock = 256;
 constexpr int kWarps = kBlock / 32;
-constexpr int kDMax = 128;              // outputs per Taylor block
+constexpr int kDMax = 128;              // outputs per Taylor job (a larger Algorithm 5.2
+                                        // block becomes several jobs from the same Z)
 constexpr int kKReg = 2;                // outputs whose running max lives in registers (the
                                         // rest use shared memory): 2 keeps the kernel at 64
                                         // registers, 4 blocks (32 warps) per SM
@@ -316,7 +317,7 @@ series_kernel(SeriesArgs a) {
     for (int k = tid; k < J.d; k += kBlock) {
       s_c1[k] = normz;
       s_coef[k] = 1.0;
-      s_step[k] = (double)(k + 1) / (double)J.d;
+      s_step[k] = (double)(J.k_off + k + 1) / (double)J.d_block;
       s_active[k] = 1;
     }
     __syncthreads();
@@ -576,7 +577,8 @@ __global__ void plan_kernel(const double* __restrict__ dp, int prec, double t0, 
                             int steps, int n0, int ring, Job* jobs, int max_jobs, int expect,
                             Ctrl* ctrl) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
-    const PlanInfo info = plan_series(dp, c_theta[prec], t0, dt, steps, n0, ring, jobs, max_jobs);
+    const PlanInfo info =
+        plan_series(dp, c_theta[prec], t0, dt, steps, n0, ring, jobs, max_jobs, kDMax);
     ctrl->njobs = info.njobs;
     if (info.njobs != expect) ctrl->error = kErrPlan;
   }
@@ -803,15 +805,60 @@ double op_bytes(const Op& op) {
   return (double)op.g.nnz_hoff * (4 + rb) + (double)op.Nt * 2 * rb;
 }
 
+// Plan figures and the algorithmic byte / flop counts of one series call, from
+// the plan and the kernel's counters (every series entry point reports these).
+void fill_series_stats(const Op& op, const PlanInfo& info, unsigned long long matvecs,
+                       unsigned long long fupdates, bool herm, qsw_series_stats* stats) {
+  const bool f32 = op.precision == QSW_C64_BULK;
+  const double vbytes = f32 ? sizeof(float2) : sizeof(double2);
+  stats->m0 = info.m0;
+  stats->s0 = info.s0;
+  stats->m_star = info.m_star;
+  stats->s = info.s;
+  stats->step_m = info.step_m;
+  stats->step_s = info.step_s;
+  stats->outputs_per_block = info.d;
+  stats->jobs = info.njobs;
+  stats->matvecs = (int64_t)matvecs;
+  stats->fupdates = (int64_t)fupdates;
+  // per job: read Z and write Khat_0; per output: one copy of Z
+  const double init_bytes =
+      (16.0 + vbytes) * (double)op.n * info.njobs + 16.0 * (double)op.n * info.outputs;
+  // the Hermitian form computes the upper triangle: (N~+1)/(2N~) of the
+  // off-diagonal terms and N~(N~+1)/2 elements
+  const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
+  const double elems = frac * (double)op.n;
+  double flops_per_matvec;
+  double wbytes = 0.0;   // global walks: pass A writes and pass B reads the W products
+  if (op.gq.active) {
+    // pass A: 8 flops per (element, entry of row j of L'); pass B: 8 per
+    // entry of rows i and j of Q and of row i of L' (complex products)
+    const double nt = op.Nt;
+    flops_per_matvec = 8.0 * nt * (double)op.gq.nnz_l +
+                       frac * 8.0 * nt * (2.0 * (double)op.gq.nnz_q + (double)op.gq.nnz_l) +
+                       5.0 * elems;
+    wbytes = 2.0 * vbytes * (double)op.gq.nl * (double)op.n;
+  } else {
+    const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
+    flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems + 4.0 * op.g.n_jumps + 5.0 * elems;
+  }
+  // one application: the operator's own data, reading the input once and
+  // writing the output once (the elements computed)
+  stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes + wbytes;
+  stats->algorithmic_bytes = (double)matvecs * stats->bytes_per_matvec +
+                             32.0 * elems * (double)fupdates + init_bytes;
+  stats->algorithmic_flops = (double)matvecs * flops_per_matvec + 7.0 * elems * fupdates;
+  stats->hermitian = herm ? 1 : 0;
+  stats->kernel_ms = 0.0;
+}
+
 void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, double* d_out,
                 double* d_pops, qsw_series_stats* stats, const OutputSink* sink) {
   cudaStream_t st = op.ctx->stream;
   const int prec = op.precision == QSW_C64_BULK ? 1 : 0;
   const double* theta = theta_table(op.precision);
   // Host copy of the plan: sizes only (the device plans for itself below).
-  const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0);
-  QSW_CHECK_ARG(info.max_d <= kDMax, QSW_ERR_INVALID_ARG,
-                "more than " + std::to_string(kDMax) + " outputs per Taylor block (steps/s too large)");
+  const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0, kDMax);
   const int ring = d_out ? 0 : info.max_d + 1;
   const bool f32 = op.precision == QSW_C64_BULK;
   const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
@@ -909,55 +956,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   if (h.error == kErrPlan)
     throw Error{QSW_ERR_CUDA, "series kernel: device plan differs from host plan"};
   if (stats) {
-    stats->m0 = info.m0;
-    stats->s0 = info.s0;
-    stats->m_star = info.m_star;
-    stats->s = info.s;
-    stats->step_m = info.step_m;
-    stats->step_s = info.step_s;
-    stats->outputs_per_block = info.d;
-    stats->jobs = info.njobs;
-    stats->matvecs = (int64_t)h.matvecs;
-    stats->fupdates = (int64_t)h.fupdates;
-    // algorithmic bytes of one application: the operator's own data, reading
-    // the input vector once and writing the output once
-    stats->bytes_per_matvec = op_bytes(op) + 2.0 * (double)op.n * vbytes;
-    std::vector<Job> jobs(info.njobs);
-    plan_series(op.dp, theta, t0, dt, steps, 1, ring, jobs.data(), info.njobs);
-    double init_bytes = 0.0;   // per block: read Z, write Khat_0 and d copies of Z
-    for (const Job& j : jobs) init_bytes += (16.0 + vbytes + 16.0 * j.d) * (double)op.n;
-    stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
-                               32.0 * (double)op.n * (double)h.fupdates + init_bytes;
-    // the Hermitian form computes the upper triangle: (N~+1)/(2N~) of the
-    // off-diagonal terms and N~(N~+1)/2 elements
-    const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
-    const double elems = frac * (double)op.n;
-    double flops_per_matvec;
-    if (op.gq.active) {
-      // pass A: 8 flops per (element, entry of row j of L'); pass B: 8 per
-      // entry of rows i and j of Q and of row i of L' (complex products)
-      const double nt = op.Nt;
-      flops_per_matvec = 8.0 * nt * (double)op.gq.nnz_l +
-                         frac * 8.0 * nt * (2.0 * (double)op.gq.nnz_q + (double)op.gq.nnz_l) +
-                         5.0 * elems;
-    } else {
-      const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
-      flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems + 4.0 * op.g.n_jumps + 5.0 * elems;
-    }
-    stats->algorithmic_flops = stats->matvecs * flops_per_matvec + 7.0 * elems * h.fupdates;
-    if (op.gq.active) {
-      // pass A writes and pass B reads the W products
-      stats->bytes_per_matvec += 2.0 * vbytes * (double)op.gq.nl * (double)op.n;
-      stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
-                                 32.0 * (double)op.n * (double)h.fupdates + init_bytes;
-    }
-    if (herm) {
-      stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes +
-                                (op.gq.active ? 2.0 * vbytes * (double)op.gq.nl * (double)op.n : 0.0);
-      stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
-                                 32.0 * elems * (double)h.fupdates + init_bytes;
-    }
-    stats->hermitian = herm ? 1 : 0;
+    fill_series_stats(op, info, h.matvecs, h.fupdates, herm, stats);
     stats->kernel_ms = ms;
   }
 }
@@ -981,7 +980,9 @@ void* g_noalloc_base[kNoAllocDevices] = {};
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Device address of g_noalloc_scratch on the current device, looked up once
-// per device (the first call on a device does this set-up).
+// per device (the first call on a device does this set-up).  The address is
+// kept for the life of the process: it assumes the device's primary context
+// lives as long (a cudaDeviceReset would leave a stale address behind).
 unsigned char* noalloc_base(int device) {
   QSW_CHECK_ARG(device >= 0 && device < kNoAllocDevices, QSW_ERR_INVALID_ARG,
                 "device index beyond the no-allocation scratch table");
@@ -1004,9 +1005,7 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
   cudaStream_t st = op.ctx->stream;
   const int prec = op.precision == QSW_C64_BULK ? 1 : 0;
   const double* theta = theta_table(op.precision);
-  const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0);
-  QSW_CHECK_ARG(info.max_d <= kDMax, QSW_ERR_INVALID_ARG,
-                "more than " + std::to_string(kDMax) + " outputs per Taylor block (steps/s too large)");
+  const PlanInfo info = plan_series(op.dp, theta, t0, dt, steps, 1, 0, nullptr, 0, kDMax);
   const int ring = d_out ? 0 : info.max_d + 1;
   const bool f32 = op.precision == QSW_C64_BULK;
   const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
@@ -1083,36 +1082,8 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
     throw Error{QSW_ERR_NOT_CONVERGED, "series kernel: grid barrier wait exceeded its limit"};
   if (h.error == kErrPlan)
     throw Error{QSW_ERR_CUDA, "series kernel: device plan differs from host plan"};
-  if (stats) {
-    // Same figures as qsw_expmv_series except kernel_ms (no timing events).
-    stats->m0 = info.m0;
-    stats->s0 = info.s0;
-    stats->m_star = info.m_star;
-    stats->s = info.s;
-    stats->step_m = info.step_m;
-    stats->step_s = info.step_s;
-    stats->outputs_per_block = info.d;
-    stats->jobs = info.njobs;
-    stats->matvecs = (int64_t)h.matvecs;
-    stats->fupdates = (int64_t)h.fupdates;
-    // outputs initialised per call: one per stage of the first state, then
-    // one per dt sub-step (steps <= s) or one per output (Algorithm 5.2)
-    const double outputs_init =
-        (double)info.s0 + (steps > 0 ? (steps <= info.s ? (double)steps * info.step_s : steps) : 0.0);
-    const double init_bytes =
-        (16.0 + vbytes) * (double)op.n * info.njobs + 16.0 * (double)op.n * outputs_init;
-    const double frac = herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
-    const double elems = frac * (double)op.n;
-    const double offdiag_terms = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps);
-    const double flops_per_matvec = 4.0 * offdiag_terms + 8.0 * elems +
-                                    4.0 * op.g.n_jumps + 5.0 * elems;
-    stats->bytes_per_matvec = op_bytes(op) + 2.0 * elems * vbytes;
-    stats->algorithmic_bytes = stats->matvecs * stats->bytes_per_matvec +
-                               32.0 * elems * (double)h.fupdates + init_bytes;
-    stats->algorithmic_flops = stats->matvecs * flops_per_matvec + 7.0 * elems * h.fupdates;
-    stats->hermitian = herm ? 1 : 0;
-    stats->kernel_ms = 0.0;
-  }
+  // the same figures as qsw_expmv_series, except kernel_ms (no timing events)
+  if (stats) fill_series_stats(op, info, h.matvecs, h.fupdates, herm, stats);
 }
 
 double probe_wait_limit(qsw_ctx* ctx) {

@@ -133,6 +133,7 @@ _SIGNATURES = {
     "qsw_probe_wait_limit": ([c_void_p, POINTER(c_double)], c_int32),
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
     "qsw_kernel_launches": ([], c_int64),
+    "qsw_device_allocations": ([], c_int64),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
     "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
     "qsw_server_wait": ([c_void_p, c_int64, c_double, POINTER(qsw_request_result)], c_int32),
@@ -476,6 +477,10 @@ def qsw_server_destroy(server) -> None:
 
 def qsw_kernel_launches() -> int:
     return int(lib().qsw_kernel_launches())
+
+
+def qsw_device_allocations() -> int:
+    return int(lib().qsw_device_allocations())
 
 
 def qsw_theta_table(precision="c128") -> np.ndarray:

@@ -46,7 +46,9 @@ def _run(ctx, w, fn, rho0, t0, dt, steps, with_out=True):
     out = (torch.full((steps + 1, w.n, 2), np.nan, dtype=torch.float64, device="cuda:0")
            if with_out else None)
     pops = torch.full((steps + 1, w.n_tilde), np.nan, dtype=torch.float64, device="cuda:0")
+    allocs0 = C.qsw_device_allocations()
     stats = getattr(C, fn)(ctx.handle, w.op, rho0, t0, dt, steps, out, pops)
+    stats["device_allocations"] = C.qsw_device_allocations() - allocs0
     torch.cuda.synchronize()
     return (None if out is None else out.cpu().numpy()), pops.cpu().numpy(), stats
 
@@ -76,8 +78,13 @@ def test_noalloc_matches_series_twice(ctx, case):
     w = _walk(ctx, _graph(gname), omega, prec, opk, src, snk)
     rho0 = _rho0(w, 11)
     ref_out, ref_pops, ref_stats = _run(ctx, w, "qsw_expmv_series", rho0, t0, dt, steps, with_out)
+    # positive control: the allocating entry point's first call on a fresh
+    # operator allocates its workspace, and the counter sees it
+    assert ref_stats["device_allocations"] > 0
     for call in range(2):
         out, pops, stats = _run(ctx, w, "qsw_expmv_series_noalloc", rho0, t0, dt, steps, with_out)
+        # the property the entry point exists for: the library allocated nothing
+        assert stats["device_allocations"] == 0, f"call {call}"
         assert np.all(np.isfinite(pops)), f"call {call}: unwritten populations"
         tol = TOL_C128 if prec == "c128" else TOL_C64_POP
         assert np.max(np.abs(pops - ref_pops)) <= tol, f"call {call}"
