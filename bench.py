@@ -57,6 +57,12 @@ def parse_args():
                     help="er1000: one walk per step (default); batch256: 256 random 4-regular "
                          "walks with 4 pure states each, complex64, one batched launch per step")
     ap.add_argument("--oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--grid-oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--batch-oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--serve-oracle-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--record-traffic", metavar="NCU_CSV",
+                    help="write profiles/series_kernel_er1000_traffic.json from an ncu --csv log")
+    ap.add_argument("--record-command", default="", help="the ncu command the CSV came from")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run one build + one series of this many output times and exit "
                          "(small case for ncu captures)")
@@ -102,11 +108,11 @@ def oracle_sample() -> dict:
     return {"seconds": sec, "steps": SAMPLE_STEPS}
 
 
-def run_oracle_subprocess() -> dict:
+def run_oracle_subprocess(flag: str = "--oracle-sample") -> dict:
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-sample"],
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), flag],
                          capture_output=True, text=True, env=env, cwd=ROOT)
     if res.returncode != 0:
         raise RuntimeError("oracle sample failed:\n" + res.stderr[-2000:])
@@ -193,25 +199,63 @@ KERNEL_SOURCES = ["paper_2003_02450_gb300/csrc/series.cu", "paper_2003_02450_gb3
                   "paper_2003_02450_gb300/csrc/params.cuh", "paper_2003_02450_gb300/csrc/gqsw.cuh"]
 
 
-def series_traffic():
-    """DRAM bytes of one full-size series launch from the committed ncu summary,
-    or None when the kernel sources changed since that capture."""
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "series_kernel_er1000_traffic.json")
+
+
+def kernel_sources_sha256() -> str:
     import hashlib
-    import re
     h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def series_traffic():
+    """DRAM bytes (read + write) of one full-size series launch, from the record
+    written by `bench.py --record-traffic` out of an ncu capture, or None when
+    the kernel sources changed since that capture."""
     try:
-        for f in KERNEL_SOURCES:
-            with open(os.path.join(ROOT, f), "rb") as fh:
-                h.update(fh.read())
-        with open(os.path.join(ROOT, "profiles", "series_kernel_er1000.md")) as fh:
-            text = fh.read()
-    except OSError:
+        with open(TRAFFIC_RECORD) as fh:
+            rec = json.load(fh)
+        if rec["kernel_sources_sha256"] != kernel_sources_sha256():
+            return None
+        return int(rec["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
         return None
-    m_hash = re.search(r"kernel sources sha256: ([0-9a-f]{64})", text)
-    m_bytes = re.search(r"dram bytes per full launch: ([0-9]+)", text)
-    if not m_hash or not m_bytes or m_hash.group(1) != h.hexdigest():
-        return None
-    return int(m_bytes.group(1))
+
+
+def record_traffic(csv_path: str, command: str) -> None:
+    """Write TRAFFIC_RECORD from an ncu --csv log of the full-size bench command
+    with the metrics dram__bytes_read.sum, dram__bytes_write.sum and
+    gpu__time_duration.sum captured on the series kernel (-k regex:series_kernel)."""
+    import csv
+    rows = []
+    with open(csv_path, newline="") as fh:
+        lines = [ln for ln in fh if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        if "series_kernel" in r.get("Kernel Name", ""):
+            rows.append(r)
+    launches = {}
+    for r in rows:
+        v = float(r["Metric Value"].replace(",", ""))
+        unit = r.get("Metric Unit", "")
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+                 "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "second": 1.0}.get(unit, 1.0)
+        launches.setdefault(r["ID"], {})[r["Metric Name"]] = v * scale
+    if not launches:
+        raise SystemExit(f"no series_kernel launch in {csv_path}")
+    first = launches[sorted(launches, key=int)[0]]
+    rec = {"kernel": "series_kernel (er1000 bench launch: 50 outputs, complex128, matrix-free)",
+           "kernel_sources_sha256": kernel_sources_sha256(),
+           "dram_bytes_read": int(first["dram__bytes_read.sum"]),
+           "dram_bytes_write": int(first["dram__bytes_write.sum"]),
+           "dram_bytes_per_launch": int(first["dram__bytes_read.sum"] + first["dram__bytes_write.sum"]),
+           "gpu_time_duration_ms": first["gpu__time_duration.sum"] * 1e3,
+           "command": command}
+    with open(TRAFFIC_RECORD, "w") as fh:
+        json.dump(rec, fh, indent=1)
+    print(json.dumps(rec))
 
 
 def csr_equivalent(nnz: int, n: int, peak_gbs: float, kernel_ms: float, matvecs: int) -> dict:
@@ -650,6 +694,46 @@ def est_cpu_baseline(walks, omegas):
                       f"{sec:.1f} s"}
 
 
+def batch_oracle_sample(count: int = 6) -> dict:
+    """Oracle as it stands on the first `count` walks of the batch256 workload:
+    per walk the Kronecker superoperator and Algorithm 5.2 on its n x 4 block of
+    initial states over 10 steps of 0.2 (populations of every output)."""
+    import numpy as np
+    from oracle import expmv, graph, superop
+    from paper_2003_02450_gb300 import workloads as W
+    walks = W.batch_regular(count=256)[:count]
+    t = time.perf_counter()
+    for g, omega, states in walks:
+        walk = graph.lqsw_walk(graph.adjacency(g))
+        L = superop.superoperator(walk, omega)
+        B = np.stack([W.vec(x) for x in states], axis=1)
+        X = expmv.expmv_series(L, B, 0.0, 0.2, 10, n0=4)
+        np.real(X[:, np.arange(g.n) * (g.n + 1), :])
+    return {"seconds": time.perf_counter() - t, "walks": count}
+
+
+def serve_oracle_sample(budget_s: float = 20.0) -> dict:
+    """Oracle as it stands replaying the serve2000 request list serially from the
+    start (Kronecker superoperator + Algorithm 5.2 per request) until
+    `budget_s` seconds have passed."""
+    import numpy as np
+    from oracle import expmv, graph, superop
+    from paper_2003_02450_gb300 import workloads as W
+    specs = W.serve_requests(count=2000)
+    t = time.perf_counter()
+    done = 0
+    for sp in specs:
+        g = W.erdos_renyi_mean_degree(sp["n"], 8.0, sp["graph_seed"])
+        walk = graph.lqsw_walk(graph.adjacency(g))
+        L = superop.superoperator(walk, sp["omega"])
+        X = expmv.expmv_series(L, W.vec(W.basis_state(sp["n"], 0)), 0.0, sp["dt"], sp["steps"])
+        superop.populations(X, walk.n_tilde)
+        done += 1
+        if time.perf_counter() - t >= budget_s:
+            break
+    return {"seconds": time.perf_counter() - t, "requests": done}
+
+
 def run_batch_workload(args):
     """256 random 4-regular walks (N ~ U{16..512}), omega ~ U(0,1), 4 random pure
     states each, 10 steps of dt = 0.2.  One step = build the 256 operators from
@@ -709,7 +793,38 @@ def run_batch_workload(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     single_ms = e0.elapsed_time(e1)
+    # the same single-walk calls with every operator (and its 1-norm series)
+    # built before the timed region: the series alone, no build cost at all
+    ops1 = [C.qsw_build_superoperator(ctx, g, None, om, precision="c128") for g, om, _ in walks]
+
+    def single_series():
+        for (g, _, _), op, rho in zip(walks, ops1, rhos):
+            n = g.n * g.n
+            for c in range(n0):
+                C.qsw_expmv_series(ctx, op, rho[c * n:(c + 1) * n], 0.0, dt, q, None, out1[g.n])
+    single_series()
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    single_series()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    series_only_ms = e0.elapsed_time(e1)
+    for op in ops1:
+        C.qsw_op_destroy(op)
     C.qsw_destroy(ctx)
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            smp = run_oracle_subprocess("--batch-oracle-sample")
+            cpu = {"value": smp["walks"] / smp["seconds"], "unit": "walks/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"FP64 numpy/scipy oracle, single thread, on a fixed subset: the first "
+                             f"{smp['walks']} of the 256 walks (Kronecker superoperator + "
+                             f"Algorithm 5.2 on the n x 4 block, 10 steps), {smp['seconds']:.1f} s; "
+                             f"walks/s extrapolated from that subset"}
+        except Exception as exc:   # reported, not fatal
+            cpu = {"value": None, "unit": "walks/s", "cores": 1, "kind": "oracle",
+                   "error": str(exc)[:300]}
     s0 = stats[-1]
     line = {"metric": "walks/s (256 random 4-regular walks x 4 pure states, 10 steps, batched)",
             "value": len(walks) * 1000.0 / ms, "unit": "walks/s", "n_gpus": 1,
@@ -721,8 +836,14 @@ def run_batch_workload(args):
                        "steps": q, "dt": dt, "clusters": s0["clusters"]},
             "batch": {"norms_ms": s0["norms_ms"], "series_ms": s0["series_ms"],
                       "matvecs": s0["matvecs"], "fupdates": s0["fupdates"]},
-            "single_walk_c128": {"ms": single_ms, "walks_per_s": len(walks) * 1000.0 / single_ms},
-            "gpu_launches": launches, "clocks": clocks}
+            "single_walk_c128": {"ms": single_ms, "walks_per_s": len(walks) * 1000.0 / single_ms,
+                                 "what": "per walk: build (incl. its 1-norm series) + one "
+                                         "qsw_expmv_series per initial state"},
+            "single_walk_c128_series_only": {
+                "ms": series_only_ms, "walks_per_s": len(walks) * 1000.0 / series_only_ms,
+                "what": "the same series calls with every operator built before the timed "
+                        "region (no build or norm cost, unlike the batched step)"},
+            "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks}
     print(json.dumps(line))
 
 
@@ -778,6 +899,18 @@ def run_serve_workload(args):
     loads = {}
     for load in (0.5, 0.9):
         loads[str(load)] = run(load * cap["throughput_rps"])
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            smp = run_oracle_subprocess("--serve-oracle-sample")
+            cpu = {"value": smp["requests"] / smp["seconds"], "unit": "requests/s", "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"FP64 numpy/scipy oracle, single thread, replaying the request list "
+                             f"serially from its start: {smp['requests']} requests in "
+                             f"{smp['seconds']:.1f} s"}
+        except Exception as exc:   # reported, not fatal
+            cpu = {"value": None, "unit": "requests/s", "cores": 1, "kind": "oracle",
+                   "error": str(exc)[:300]}
     line = {"metric": "served walk requests/s and p50/p99 latency (Poisson arrivals)",
             "value": cap["throughput_rps"], "unit": "requests/s", "n_gpus": 1,
             "steps": 1, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
@@ -785,21 +918,43 @@ def run_serve_workload(args):
             "data": "synthetic (seeded Erdos-Renyi digraphs, mean out-degree 8)",
             "config": {"workload": "serve2000", "requests": len(specs), "N": "log-uniform [32, 1024]",
                        "steps": "U{1..100}", "dt": 0.1, "workers": 4, "max_batch": 64},
-            "capacity": cap, "offered_load": loads}
+            "capacity": cap, "offered_load": loads, "cpu_baseline": cpu}
     print(json.dumps(line))
+
+
+def grid_oracle_sample(steps: int) -> dict:
+    """Oracle as it stands on the 45 x 45 lattice: Kronecker assembly plus
+    Algorithm 5.2 over the first `steps` output times of its grid."""
+    from oracle import expmv, graph, superop
+    from paper_2003_02450_gb300 import workloads as W
+    cfg = W.grid45("c128")
+    t = time.perf_counter()
+    walk = graph.lqsw_walk(graph.adjacency(cfg.graph))
+    L = superop.superoperator(walk, cfg.omega)
+    X = expmv.expmv_series(L, W.vec(cfg.rho0), cfg.t0, cfg.dt, steps)
+    superop.populations(X, walk.n_tilde)
+    return {"seconds": time.perf_counter() - t, "steps": steps}
 
 
 def run_grid_workload(args):
     """45 x 45 lattice (N = 2025, n = 4.1e6), omega = 0.1, rho0 = |centre><centre|,
     20 steps of dt = 0.5: complex64 bulk (FP64 sums) and complex128, whole path
-    per step (build + series + populations)."""
+    per step (build + series + populations).  The complex64 result's population
+    error is reported per output time against the FP64 oracle's stored series
+    (tests/golden/grid45_series.npz, written by the oracle alone) and against
+    the complex128 run."""
+    import numpy as np
     import torch
     from paper_2003_02450_gb300 import qsw as C
     from paper_2003_02450_gb300 import workloads as W
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
     ctx = C.qsw_create(0, stream.cuda_stream)
-    out = {}
+    out, final_pops = {}, {}
+    fp64_peak = fp64_peak_tflops()
+    peak_gbs, peak_kind = measured_peak_gbs()
+    sampler = ClockSampler(0)
+    sampler.start()
     for prec in ("c64", "c128"):
         cfg = W.grid45(prec)
         rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
@@ -808,7 +963,9 @@ def run_grid_workload(args):
         def step():
             op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec)
             st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, cfg.steps, None, pops)
+            info = C.qsw_op_info(ctx, op)
             C.qsw_op_destroy(op)
+            st["nnz"] = info["nnz"]
             return st
         for _ in range(max(1, args.warmup)):
             step()
@@ -820,15 +977,56 @@ def run_grid_workload(args):
         torch.cuda.synchronize(dev)
         ms = e0.elapsed_time(e1) / args.steps
         s0 = stats[-1]
+        kms = statistics.mean(x["kernel_ms"] for x in stats)
+        tf = s0["algorithmic_flops"] / (kms * 1e-3) / 1e12
         out[prec] = {"time_steps_per_s": cfg.steps * 1000.0 / ms, "ms_per_step": ms,
-                     "series_kernel_ms": s0["kernel_ms"], "matvecs": s0["matvecs"],
-                     "m_star": s0["m_star"], "s": s0["s"],
-                     "achieved_gbs": s0["algorithmic_bytes"] / (s0["kernel_ms"] * 1e-3) / 1e9,
-                     "achieved_tflops": s0["algorithmic_flops"] / (s0["kernel_ms"] * 1e-3) / 1e12}
+                     "series_kernel_ms": kms, "build_and_other_ms": ms - kms,
+                     "matvecs": s0["matvecs"], "m_star": s0["m_star"], "s": s0["s"],
+                     "roofline": {"bound": "alu", "pipe": "fp64" if prec == "c128" else "fp32 + fp64",
+                                  "achieved_tflops": tf, "fp64_peak_tflops": fp64_peak,
+                                  "frac_of_fp64_peak": tf / fp64_peak,
+                                  "hbm_view_gbs": s0["algorithmic_bytes"] / (kms * 1e-3) / 1e9,
+                                  "hbm_peak_gbs": peak_gbs, "hbm_peak_source": peak_kind},
+                     "csr_equivalent": csr_equivalent(s0["nnz"], 2025 ** 2, peak_gbs, kms,
+                                                      s0["matvecs"])}
+        final_pops[prec] = pops.cpu().numpy()
+    clocks = sampler.stop()
     C.qsw_destroy(ctx)
+    # accuracy of the complex64 bulk result, per output time
+    acc = {}
+    try:
+        g = np.load(os.path.join(ROOT, "tests", "golden", "grid45_series.npz"))
+        e_or = np.max(np.abs(final_pops["c64"] - g["pops"]), axis=1)
+        e_c128_or = np.max(np.abs(final_pops["c128"] - g["pops"]), axis=1)
+        acc["c64_pop_err_vs_oracle_per_output"] = [float(x) for x in e_or]
+        acc["c64_pop_err_vs_oracle_max"] = float(e_or.max())
+        acc["c128_pop_err_vs_oracle_max"] = float(e_c128_or.max())
+    except OSError:
+        acc["oracle_series"] = "tests/golden/grid45_series.npz not found"
+    e_c = np.max(np.abs(final_pops["c64"] - final_pops["c128"]), axis=1)
+    acc["c64_pop_err_vs_c128_per_output"] = [float(x) for x in e_c]
+    acc["bound"] = "c64 populations <= 1e-4; c128 <= 1e-10 (tests/test_gpu_full_series.py)"
+    cpu = None
+    if not args.no_cpu_baseline:
+        try:
+            smp = run_oracle_subprocess("--grid-oracle-sample")
+            cpu = {"value": smp["steps"] / smp["seconds"], "unit": UNIT, "cores": 1,
+                   "kind": "oracle",
+                   "sample": f"FP64 numpy/scipy oracle, single thread: Kronecker superoperator of "
+                             f"the 45x45 lattice walk + Algorithm 5.2 over its first "
+                             f"{smp['steps']} output times (dt=0.5), {smp['seconds']:.1f} s"}
+        except Exception as exc:   # reported, not fatal
+            cpu = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "error": str(exc)[:300]}
     print(json.dumps({"metric": "walk time-steps/s (45x45 lattice, 20 steps of 0.5)",
-                      "value": out["c64"]["time_steps_per_s"], "unit": "time-steps/s",
-                      "config": {"workload": "grid45"}, "c64": out["c64"], "c128": out["c128"]}))
+                      "value": out["c64"]["time_steps_per_s"], "unit": "time-steps/s", "n_gpus": 1,
+                      "steps": args.steps, "warmup": args.warmup,
+                      "ms_per_step": out["c64"]["ms_per_step"], "higher_is_better": True,
+                      "dtype": "c64 bulk (complex64 terms, FP64 Taylor sums / norms / (m,s)); "
+                               "c128 beside it", "data": "synthetic (45x45 lattice)",
+                      "config": {"workload": "grid45", "N": 2025, "omega": 0.1, "dt": 0.5,
+                                 "series_steps": 20},
+                      "c64": out["c64"], "c128": out["c128"], "accuracy": acc,
+                      "cpu_baseline": cpu, "clocks": clocks}))
 
 
 def run_profile_case(q: int):
@@ -855,6 +1053,18 @@ def main():
         return
     if args.oracle_sample:
         print(json.dumps(oracle_sample()))
+        return
+    if args.grid_oracle_sample:
+        print(json.dumps(grid_oracle_sample(2)))
+        return
+    if args.batch_oracle_sample:
+        print(json.dumps(batch_oracle_sample()))
+        return
+    if args.serve_oracle_sample:
+        print(json.dumps(serve_oracle_sample()))
+        return
+    if args.record_traffic:
+        record_traffic(args.record_traffic, args.record_command)
         return
     if args.impl == "reference":
         run_reference(args)
