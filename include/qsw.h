@@ -81,6 +81,11 @@ typedef enum { QSW_OPERATOR_MATRIX_FREE = 0, QSW_OPERATOR_CSR = 1 } qsw_operator
  * qsw_expmv_series, or on the device by qsw_batch_series). */
 #define QSW_BUILD_DEFER_NORMS 0x100
 
+/* OR-ed into operator_kind: do not autotune this operator's schedule (a
+ * QSW_OPERATOR_CSR operator then keeps the row-length heuristic's lanes per
+ * row instead of the tuned value; see qsw_op_schedule). */
+#define QSW_BUILD_FIXED_SCHEDULE 0x200
+
 typedef struct qsw_ctx qsw_ctx;   /* device + stream + workspace cache */
 typedef struct qsw_op qsw_op;     /* one assembled superoperator L~ */
 
@@ -484,6 +489,32 @@ int64_t qsw_kernel_launches(void);
  * library has made in the calling process, all contexts.  Pure host call; a
  * caller can read it around a call to see whether that call allocated. */
 int64_t qsw_device_allocations(void);
+
+/* ------------------------------------------------------------ autotuning
+ *
+ * Not in the paper (a schedule choice of this library).  The CSR sweep of
+ * the series kernel runs TPR lanes per row of L~ (1, 2, 4, 8, 16 or 32), which
+ * sets the cost of its shuffle reductions and how the operator stream is
+ * coalesced.  The first qsw_expmv_series on a QSW_OPERATOR_CSR operator
+ * (without QSW_BUILD_FIXED_SCHEDULE) looks up the device's choice for its
+ * (precision, row-length bucket, size bucket); when there is none it times
+ * every candidate with the series kernel on that operator (eight Taylor terms
+ * from a fixed vector, about 20 short launches, plus two Taylor-term vectors
+ * of workspace), keeps the fastest for the life of the process and uses it
+ * for every later operator in that bucket.  Results depend on the choice
+ * only through the summation order within a row (well inside the 1e-10
+ * parity bound).  The no-allocation entry point never tunes: it uses the
+ * operator's current value. */
+
+/* Number of schedule measurements (one per tuned bucket) made in this
+ * process.  Pure host call. */
+int64_t qsw_tune_measurements(void);
+/* Forget every tuned schedule (the next CSR operator of each bucket is
+ * measured again).  Pure host call; not safe against concurrent series. */
+void qsw_tune_reset(void);
+/* The operator's CSR lanes per row (0 for a matrix-free operator): the
+ * heuristic value until its first series, the tuned value after it. */
+qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row);
 
 /* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
  * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor

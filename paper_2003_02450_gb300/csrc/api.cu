@@ -199,7 +199,9 @@ void rebuild(Op& op, bool defer_norms) {
     qsw::compute_norms(op, &op.L, &LH);
     LH = qsw::Csr{};
     if (op.precision == QSW_C64_BULK) qsw::to_fp32(op, op.L);
-    op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
+    // the length heuristic until the first series tunes it (kept across
+    // set_omega: the structure does not change)
+    if (!op.tpr_fixed || op.tpr <= 0) op.tpr = qsw::choose_tpr((double)op.L.nnz / (double)op.n);
   } else if (!defer_norms) {
     qsw::compute_norms(op, nullptr, nullptr);
   }
@@ -273,7 +275,8 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
     QSW_CHECK_ARG(precision == QSW_C128 || precision == QSW_C64_BULK, QSW_ERR_INVALID_ARG,
                   "unknown precision");
     const bool defer = (operator_kind & QSW_BUILD_DEFER_NORMS) != 0;
-    operator_kind &= ~QSW_BUILD_DEFER_NORMS;
+    const bool fixed_schedule = (operator_kind & QSW_BUILD_FIXED_SCHEDULE) != 0;
+    operator_kind &= ~(QSW_BUILD_DEFER_NORMS | QSW_BUILD_FIXED_SCHEDULE);
     QSW_CHECK_ARG(operator_kind == QSW_OPERATOR_MATRIX_FREE || operator_kind == QSW_OPERATOR_CSR,
                   QSW_ERR_INVALID_ARG, "unknown operator kind");
     QSW_CHECK_ARG(!defer || operator_kind == QSW_OPERATOR_MATRIX_FREE, QSW_ERR_INVALID_ARG,
@@ -299,6 +302,10 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
     op->ctx = ctx;
     op->precision = precision;
     op->opkind = operator_kind;
+    if (fixed_schedule) {   // keep the length heuristic's lanes per row
+      op->tpr_fixed = true;
+      op->tpr = 0;
+    }
     op->omega = omega;
     op->N = G->n;
     op->Nt = (int)Nt;
@@ -694,6 +701,17 @@ qsw_status qsw_populations(const qsw_op* h, const double* d_rho, int32_t count, 
 int64_t qsw_kernel_launches(void) { return qsw::g_launches.load(); }
 
 int64_t qsw_device_allocations(void) { return qsw::g_device_allocs.load(); }
+
+int64_t qsw_tune_measurements(void) { return qsw::tune_measurements(); }
+
+void qsw_tune_reset(void) { qsw::tune_reset(); }
+
+qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row) {
+  if (!op || !csr_lanes_per_row) return QSW_ERR_INVALID_ARG;
+  const Op* o = reinterpret_cast<const Op*>(op);
+  *csr_lanes_per_row = o->opkind == QSW_OPERATOR_CSR ? o->tpr : 0;
+  return QSW_OK;
+}
 
 qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,

@@ -111,6 +111,7 @@ struct Op {
   double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
   DevBuf dp_dev;
   int tpr = 8;     // SpMV threads per row
+  bool tpr_fixed = false;   // set: keep tpr (tuned, or QSW_BUILD_FIXED_SCHEDULE)
   bool norms_ready = false;
 
   // series workspace
@@ -162,6 +163,9 @@ template <class R> struct MfOp;
 template <class R> MfOp<R> make_mf(const Op& op, bool adjoint);
 void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
 int choose_tpr(double avg_row);
+int tuned_csr_tpr(Op& op);       // autotuned lanes per row (cached per device and bucket)
+long long tune_measurements();   // schedule measurements made in this process
+void tune_reset();               // forget every tuned schedule
 // batch.cu
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,

@@ -29,7 +29,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <map>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -205,8 +207,6 @@ template <class VT> struct Epilogue {
   long long n;
   VT* knext;
   int out0, d;
-  double coef[kKReg];
-  bool own[kKReg];
   unsigned long long kmax;
   unsigned long long fmax[kKReg];
   const double* s_coef;
@@ -223,11 +223,13 @@ template <class VT> struct Epilogue {
     const double dx = (double)yx, dy = (double)yy;
 #pragma unroll
     for (int u = 0; u < kKReg; ++u) {
-      if (own[u]) {
+      // coefficients and activity come from shared memory (broadcast reads):
+      // keeping copies in registers measured slower at this register budget
+      if (u < d && s_active[u]) {
         double2* F = slot(out0 + u) + r;
         double2 f = __ldcg(F);
-        f.x = fma(coef[u], dx, f.x);
-        f.y = fma(coef[u], dy, f.y);
+        f.x = fma(s_coef[u], dx, f.x);
+        f.y = fma(s_coef[u], dy, f.y);
         *F = f;
         fmax[u] = umax64(fmax[u], NormKey<VT>::f(f.x, f.y));
       }
@@ -343,11 +345,7 @@ series_kernel(SeriesArgs a) {
       ep.s_fmax_extra = s_fmax_extra;
       ep.kmax = 0;
 #pragma unroll
-      for (int u = 0; u < kKReg; ++u) {
-        ep.own[u] = u < J.d && s_active[u];
-        ep.coef[u] = ep.own[u] ? s_coef[u] : 0.0;
-        ep.fmax[u] = 0;
-      }
+      for (int u = 0; u < kKReg; ++u) ep.fmax[u] = 0;
 
       if (OPK == kOpGlobal || OPK == kOpGlobalHerm) {
         // ---- global walk: pass A (W_k = K L'_k^dag, every element), a grid
@@ -428,46 +426,64 @@ series_kernel(SeriesArgs a) {
           }
         }
       } else {
-        // ---- CSR sweep: TPR lanes per row, warp-uniform row loop
+        // ---- CSR sweep: TPR lanes per row.  A warp owns 32 consecutive rows and
+        // covers them in TPR rounds of 32 / TPR rows; after each round's
+        // reduction, row rb + L's sum moves to lane L, so the epilogue (FP64
+        // output updates and norms) runs on all 32 lanes instead of one lane
+        // per row.
         const VT* __restrict__ val = static_cast<const VT*>(a.val);
         const int* __restrict__ col = a.col;
         const int* __restrict__ rowptr = a.rowptr;
         const int glane = lane % TPR;
         constexpr int kGpw = 32 / TPR;
         const long long wglobal = gthread / 32;
-        const long long rstride = (long long)gridDim.x * kWarps * kGpw;
-        for (long long rb = wglobal * kGpw; rb < a.n; rb += rstride) {
-          const long long r = rb + lane / TPR;
-          const bool valid = r < a.n;
-          const int e0 = valid ? rowptr[r] : 0;
-          const int e1 = valid ? rowptr[r + 1] : 0;
-          R ax = 0, ay = 0;
-          int e = e0 + glane;
-          for (; e + TPR < e1; e += 2 * TPR) {
-            const int c0 = __ldcs(col + e);
-            const int c1 = __ldcs(col + e + TPR);
-            const VT v0 = __ldcs(val + e);
-            const VT v1 = __ldcs(val + e + TPR);
-            const VT x0 = __ldcg(kcur + c0);
-            const VT x1 = __ldcg(kcur + c1);
-            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
-            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
-            ax = fma(v1.x, x1.x, fma(-v1.y, x1.y, ax));
-            ay = fma(v1.x, x1.y, fma(v1.y, x1.x, ay));
-          }
-          if (e < e1) {
-            const int c0 = __ldcs(col + e);
-            const VT v0 = __ldcs(val + e);
-            const VT x0 = __ldcg(kcur + c0);
-            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
-            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
-          }
+        const long long rstride = (long long)gridDim.x * kWarps * 32;
+        for (long long rb = wglobal * 32; rb < a.n; rb += rstride) {
+          R mx = 0, my = 0;   // the sums of row rb + lane
 #pragma unroll
-          for (int o = TPR / 2; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o, TPR);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o, TPR);
+          for (int q = 0; q < TPR; ++q) {
+            const long long r = rb + q * kGpw + lane / TPR;
+            const bool valid = r < a.n;
+            const int e0 = valid ? rowptr[r] : 0;
+            const int e1 = valid ? rowptr[r + 1] : 0;
+            R ax = 0, ay = 0;
+            int e = e0 + glane;
+            for (; e + TPR < e1; e += 2 * TPR) {
+              const int c0 = __ldcs(col + e);
+              const int c1 = __ldcs(col + e + TPR);
+              const VT v0 = __ldcs(val + e);
+              const VT v1 = __ldcs(val + e + TPR);
+              const VT x0 = __ldcg(kcur + c0);
+              const VT x1 = __ldcg(kcur + c1);
+              ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+              ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+              ax = fma(v1.x, x1.x, fma(-v1.y, x1.y, ax));
+              ay = fma(v1.x, x1.y, fma(v1.y, x1.x, ay));
+            }
+            if (e < e1) {
+              const int c0 = __ldcs(col + e);
+              const VT v0 = __ldcs(val + e);
+              const VT x0 = __ldcg(kcur + c0);
+              ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+              ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+            }
+#pragma unroll
+            for (int o = TPR / 2; o > 0; o >>= 1) {
+              ax += __shfl_xor_sync(0xffffffffu, ax, o, TPR);
+              ay += __shfl_xor_sync(0xffffffffu, ay, o, TPR);
+            }
+            // every lane of a group holds its row's sum; lane L of this round's
+            // range takes row rb + L from group L - q kGpw
+            const int src = ((lane - q * kGpw) & (kGpw - 1)) * TPR;
+            const R sx = __shfl_sync(0xffffffffu, ax, src);
+            const R sy = __shfl_sync(0xffffffffu, ay, src);
+            if (lane / kGpw == q) {
+              mx = sx;
+              my = sy;
+            }
           }
-          if (valid && glane == 0) ep.consume(r, ax * rscale, ay * rscale);
+          const long long r = rb + lane;
+          if (r < a.n) ep.consume(r, mx * rscale, my * rscale);
         }
       }
 
@@ -702,7 +718,7 @@ cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* gr
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const long long want =
-      OPK == kOpCsr ? ((long long)a.n * TPR + kBlock - 1) / kBlock
+      OPK == kOpCsr ? ((long long)a.n + 32 * kWarps - 1) / (32 * kWarps)   // 32 rows per warp
                     : (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps;
   const long long maxg = (long long)per_sm * sms;
   const int grid = (int)std::max<long long>(1, std::min(want, maxg));
@@ -724,6 +740,8 @@ cudaError_t launch_series_op(const Op& op, int tpr, bool herm, const SeriesArgs&
     return herm ? launch_series<VT, kOpMatfreeHerm, 1>(a, sms, st, g)
                 : launch_series<VT, kOpMatfree, 1>(a, sms, st, g);
   switch (tpr) {
+    case 1: return launch_series<VT, kOpCsr, 1>(a, sms, st, g);
+    case 2: return launch_series<VT, kOpCsr, 2>(a, sms, st, g);
     case 4: return launch_series<VT, kOpCsr, 4>(a, sms, st, g);
     case 8: return launch_series<VT, kOpCsr, 8>(a, sms, st, g);
     case 16: return launch_series<VT, kOpCsr, 16>(a, sms, st, g);
@@ -733,11 +751,134 @@ cudaError_t launch_series_op(const Op& op, int tpr, bool herm, const SeriesArgs&
 
 }  // namespace
 
-int choose_tpr(double avg_row) {
-  if (avg_row <= 12) return 4;
-  if (avg_row <= 24) return 8;
-  if (avg_row <= 56) return 16;
-  return 32;
+// Lanes per row without tuning: 2 was fastest on both measured superoperators
+// (the 45 x 45 lattice, ~9 entries per row, complex64; the ER-1000 walk, ~40
+// entries per row, complex128); very long rows get 4.
+int choose_tpr(double avg_row) { return avg_row <= 96 ? 2 : 4; }
+
+// ------------------------------------------------ autotuned CSR lanes per row
+// The CSR sweep's lanes per row (TPR) set the cost of the shuffle reduction and
+// how the operator stream is coalesced; the best value depends on the row
+// lengths, the precision and the size, and on the part.  The first CSR series
+// on a device for a (precision, row-length bucket, size bucket) times every
+// candidate with the series kernel itself on that operator (one job of
+// kTuneTerms Taylor terms from a fixed vector, tolerance 0 so that every
+// candidate runs the same terms, a warm-up launch then two timed launches) and
+// keeps the fastest for the life of the process.  Results depend on TPR only
+// through the summation order of each row.
+namespace {
+
+constexpr int kTuneTerms = 8;
+constexpr int kTprCandidates[] = {1, 2, 4, 8, 16, 32};
+
+struct TuneKey {
+  int device, precision, row_bucket, n_bucket;
+  bool operator<(const TuneKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (precision != o.precision) return precision < o.precision;
+    if (row_bucket != o.row_bucket) return row_bucket < o.row_bucket;
+    return n_bucket < o.n_bucket;
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, int> g_tune_tpr;
+std::atomic<long long> g_tune_measurements{0};
+
+__global__ void tune_fill_kernel(long long n, double2* __restrict__ x) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x)
+    x[e] = make_double2(1.0 / (1.0 + (double)(e % 97)), 1.0 / (2.0 + (double)(e % 89)));
+}
+
+TuneKey csr_tune_key(const Op& op) {
+  const double avg = op.n > 0 ? (double)op.L.nnz / (double)op.n : 1.0;
+  return TuneKey{op.ctx->device, (int)op.precision, (int)floor(2.0 * log2(avg > 1.0 ? avg : 1.0)),
+                 (int)floor(log2((double)(op.n > 1 ? op.n : 1)))};
+}
+
+}  // namespace
+
+long long tune_measurements() { return g_tune_measurements.load(); }
+
+void tune_reset() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune_tpr.clear();
+}
+
+int tuned_csr_tpr(Op& op) {
+  const TuneKey key = csr_tune_key(op);
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_tpr.find(key);
+    if (it != g_tune_tpr.end()) return it->second;
+  }
+  cudaStream_t st = op.ctx->stream;
+  const bool f32 = op.precision == QSW_C64_BULK;
+  const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
+  DevBuf x, kbuf, slot, ctrl, job;
+  x.alloc(sizeof(double2) * (size_t)op.n);
+  kbuf.alloc(2 * vbytes * (size_t)op.n);
+  slot.alloc(sizeof(double2) * (size_t)op.n);
+  ctrl.alloc(sizeof(Ctrl));
+  job.alloc(sizeof(Job));
+  QSW_LAUNCH tune_fill_kernel<<<grid_for(op.n, 256, 4096), 256, 0, st>>>(op.n, x.as<double2>());
+  QSW_CUDA_TRY(cudaGetLastError());
+  Job j{};
+  j.z_slot = -1;
+  j.d = 1;
+  j.m = kTuneTerms;
+  j.d_block = 1;
+  j.hspan = op.dp[0] > 0.0 ? 1.0 / op.dp[0] : 1.0;   // terms shrink: no overflow
+  QSW_CUDA_TRY(cudaMemcpyAsync(job.p, &j, sizeof(Job), cudaMemcpyHostToDevice, st));
+  SeriesArgs a{};
+  a.n = (int)op.n;
+  a.nt = op.Nt;
+  a.rowptr = op.L.rowptr.as<int>();
+  a.col = op.L.col.as<int>();
+  a.val = op.L.val.p;
+  a.k0 = kbuf.p;
+  a.k1 = static_cast<char*>(kbuf.p) + vbytes * (size_t)op.n;
+  a.rho0 = x.as<double2>();
+  a.slots = slot.as<double2>();
+  a.jobs = job.as<Job>();
+  a.njobs = 1;
+  a.ctrl = ctrl.as<Ctrl>();
+  a.tol = 0.0;
+  cudaEvent_t e0, e1;
+  QSW_CUDA_TRY(cudaEventCreate(&e0));
+  QSW_CUDA_TRY(cudaEventCreate(&e1));
+  int best = op.tpr;
+  float best_ms = 0.f;
+  for (int tpr : kTprCandidates) {
+    float tmin = 0.f;
+    for (int rep = 0; rep < 3; ++rep) {
+      QSW_CUDA_TRY(cudaMemsetAsync(ctrl.p, 0, sizeof(Ctrl), st));
+      QSW_CUDA_TRY(cudaEventRecord(e0, st));
+      int grid = 0;
+      QSW_CUDA_TRY(f32 ? launch_series_op<float2>(op, tpr, false, a, op.ctx->num_sms, st, &grid)
+                       : launch_series_op<double2>(op, tpr, false, a, op.ctx->num_sms, st, &grid));
+      QSW_CUDA_TRY(cudaEventRecord(e1, st));
+      QSW_CUDA_TRY(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      QSW_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (rep == 1 || (rep > 1 && ms < tmin)) tmin = ms;
+    }
+    Ctrl h{};
+    QSW_CUDA_TRY(cudaMemcpyAsync(&h, ctrl.p, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));
+    QSW_CUDA_TRY(cudaStreamSynchronize(st));
+    if (h.error != kErrNone)
+      throw Error{QSW_ERR_NOT_CONVERGED, "CSR schedule tuning: grid barrier wait exceeded its limit"};
+    if (best_ms == 0.f || tmin < best_ms) {
+      best_ms = tmin;
+      best = tpr;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  g_tune_measurements.fetch_add(1, std::memory_order_relaxed);
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  return g_tune_tpr.emplace(key, best).first->second;   // a concurrent tuner may have won
 }
 
 void upload_theta_batch();
@@ -862,6 +1003,10 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   const int ring = d_out ? 0 : info.max_d + 1;
   const bool f32 = op.precision == QSW_C64_BULK;
   const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
+  if (op.opkind == QSW_OPERATOR_CSR && !op.tpr_fixed) {   // first CSR series: tuned schedule
+    op.tpr = tuned_csr_tpr(op);
+    op.tpr_fixed = true;
+  }
   op.kbuf.alloc(2 * vbytes * (size_t)op.n);
   if (!d_out) op.ring.alloc(sizeof(double2) * (size_t)op.n * ring);
   op.jobs.alloc(sizeof(Job) * std::max(1, info.njobs));

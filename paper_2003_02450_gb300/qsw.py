@@ -75,6 +75,7 @@ class qsw_batch_stats(ctypes.Structure):
 
 
 QSW_BUILD_DEFER_NORMS = 0x100
+QSW_BUILD_FIXED_SCHEDULE = 0x200
 NOALLOC_SCRATCH_BYTES = 16 << 20   # QSW_NOALLOC_SCRATCH_BYTES
 
 
@@ -134,6 +135,9 @@ _SIGNATURES = {
     "qsw_theta_table": ([c_int32, POINTER(c_double)], c_int32),
     "qsw_kernel_launches": ([], c_int64),
     "qsw_device_allocations": ([], c_int64),
+    "qsw_tune_measurements": ([], c_int64),
+    "qsw_tune_reset": ([], None),
+    "qsw_op_schedule": ([c_void_p, POINTER(c_int32)], c_int32),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
     "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
     "qsw_server_wait": ([c_void_p, c_int64, c_double, POINTER(qsw_request_result)], c_int32),
@@ -253,13 +257,15 @@ def qsw_last_error(ctx) -> str:
 
 
 def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(),
-                            precision="c128", operator="matfree", defer_norms: bool = False):
+                            precision="c128", operator="matfree", defer_norms: bool = False,
+                            fixed_schedule: bool = False):
     g = _as_csr(G)
     h = _as_csr(H)
     src, nsrc = _ports(sources)
     snk, nsnk = _ports(sinks)
     prec = PRECISIONS.get(precision, precision)
-    kind = OPERATORS.get(operator, operator) | (QSW_BUILD_DEFER_NORMS if defer_norms else 0)
+    kind = (OPERATORS.get(operator, operator) | (QSW_BUILD_DEFER_NORMS if defer_norms else 0)
+            | (QSW_BUILD_FIXED_SCHEDULE if fixed_schedule else 0))
     op = c_void_p()
     st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
                                        src, nsrc, snk, nsnk, int(prec), int(kind), byref(op))
@@ -481,6 +487,20 @@ def qsw_kernel_launches() -> int:
 
 def qsw_device_allocations() -> int:
     return int(lib().qsw_device_allocations())
+
+
+def qsw_tune_measurements() -> int:
+    return int(lib().qsw_tune_measurements())
+
+
+def qsw_tune_reset() -> None:
+    lib().qsw_tune_reset()
+
+
+def qsw_op_schedule(op) -> int:
+    v = c_int32()
+    _check(lib().qsw_op_schedule(op, byref(v)))
+    return v.value
 
 
 def qsw_theta_table(precision="c128") -> np.ndarray:
