@@ -63,6 +63,11 @@ def parse_args():
     ap.add_argument("--record-traffic", metavar="NCU_CSV",
                     help="write profiles/series_kernel_er1000_traffic.json from an ncu --csv log")
     ap.add_argument("--record-command", default="", help="the ncu command the CSV came from")
+    ap.add_argument("--profile-workload", default="er1000", choices=["er1000", "grid45"],
+                    help="--profile-steps case: the ER-1000 walk or the 45x45 lattice")
+    ap.add_argument("--profile-c128", action="store_true", help="grid45 profile case in complex128")
+    ap.add_argument("--profile-fixed", action="store_true",
+                    help="profile case without schedule tuning (QSW_BUILD_FIXED_SCHEDULE)")
     ap.add_argument("--profile-steps", type=int, default=0,
                     help="run one build + one series of this many output times and exit "
                          "(small case for ncu captures)")
@@ -240,7 +245,8 @@ def record_traffic(csv_path: str, command: str) -> None:
     for r in rows:
         v = float(r["Metric Value"].replace(",", ""))
         unit = r.get("Metric Unit", "")
-        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9,
+        scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "B": 1, "KB": 1e3,
+                 "MB": 1e6, "GB": 1e9, "ns": 1e-9, "us": 1e-6, "ms": 1e-3, "s": 1.0,
                  "nsecond": 1e-9, "usecond": 1e-6, "msecond": 1e-3, "second": 1.0}.get(unit, 1.0)
         launches.setdefault(r["ID"], {})[r["Metric Name"]] = v * scale
     if not launches:
@@ -961,9 +967,11 @@ def run_grid_workload(args):
         pops = torch.empty((cfg.steps + 1, 2025), dtype=torch.float64, device=dev)
 
         def step():
-            op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec)
+            op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec,
+                                           operator=args.operator)
             st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, cfg.steps, None, pops)
             info = C.qsw_op_info(ctx, op)
+            st["lanes_per_row"] = C.qsw_op_schedule(op)
             C.qsw_op_destroy(op)
             st["nnz"] = info["nnz"]
             return st
@@ -982,11 +990,17 @@ def run_grid_workload(args):
         out[prec] = {"time_steps_per_s": cfg.steps * 1000.0 / ms, "ms_per_step": ms,
                      "series_kernel_ms": kms, "build_and_other_ms": ms - kms,
                      "matvecs": s0["matvecs"], "m_star": s0["m_star"], "s": s0["s"],
-                     "roofline": {"bound": "alu", "pipe": "fp64" if prec == "c128" else "fp32 + fp64",
+                     "operator": args.operator,
+                     "roofline": {"bound": "alu" if args.operator == "matfree" or prec == "c128" else "hbm",
+                                  "pipe": "fp64" if prec == "c128" else "fp32 + fp64",
                                   "achieved_tflops": tf, "fp64_peak_tflops": fp64_peak,
                                   "frac_of_fp64_peak": tf / fp64_peak,
                                   "hbm_view_gbs": s0["algorithmic_bytes"] / (kms * 1e-3) / 1e9,
-                                  "hbm_peak_gbs": peak_gbs, "hbm_peak_source": peak_kind},
+                                  "hbm_frac": s0["algorithmic_bytes"] / (kms * 1e-3) / 1e9 / peak_gbs,
+                                  "hbm_peak_gbs": peak_gbs, "hbm_peak_source": peak_kind,
+                                  "algorithmic_bytes_per_launch": s0["algorithmic_bytes"],
+                                  "bytes_per_term_spmv": s0["bytes_per_matvec"]},
+                     "csr_lanes_per_row": s0["lanes_per_row"] or None,
                      "csr_equivalent": csr_equivalent(s0["nnz"], 2025 ** 2, peak_gbs, kms,
                                                       s0["matvecs"])}
         final_pops[prec] = pops.cpu().numpy()
@@ -1024,32 +1038,45 @@ def run_grid_workload(args):
                       "dtype": "c64 bulk (complex64 terms, FP64 Taylor sums / norms / (m,s)); "
                                "c128 beside it", "data": "synthetic (45x45 lattice)",
                       "config": {"workload": "grid45", "N": 2025, "omega": 0.1, "dt": 0.5,
-                                 "series_steps": 20},
+                                 "series_steps": 20, "operator": args.operator},
                       "c64": out["c64"], "c128": out["c128"], "accuracy": acc,
                       "cpu_baseline": cpu, "clocks": clocks}))
 
 
-def run_profile_case(q: int):
+def run_profile_case(args):
+    """One series call for profilers: the ER-1000 walk (complex128) or the 45 x 45
+    lattice (--profile-workload grid45, complex64 bulk unless --profile-c128),
+    over the first --profile-steps output times, with --operator."""
     import torch
     from paper_2003_02450_gb300 import qsw as C
     from paper_2003_02450_gb300 import workloads as W
-    cfg = W.er1000()
+    q = args.profile_steps
+    if args.profile_workload == "grid45":
+        prec = "c128" if args.profile_c128 else "c64"
+        cfg = W.grid45(prec)
+    else:
+        prec = "c128"
+        cfg = W.er1000()
     dev = torch.device("cuda", 0)
     ctx = C.qsw_create(0, torch.cuda.current_stream(dev).cuda_stream)
     rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
     out = torch.empty((q + 1, cfg.graph.n ** 2), dtype=torch.complex128, device=dev)
-    op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega)
+    op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec,
+                                   operator=args.operator, fixed_schedule=args.profile_fixed)
     st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, None)
+    lanes = C.qsw_op_schedule(op)
     C.qsw_op_destroy(op)
     C.qsw_destroy(ctx)
-    print(json.dumps({"profile_case": WORKLOAD, "series_steps": q, "matvecs": st["matvecs"],
-                      "kernel_ms": st["kernel_ms"], "algorithmic_bytes": st["algorithmic_bytes"]}))
+    print(json.dumps({"profile_case": cfg.name, "precision": prec, "operator": args.operator,
+                      "series_steps": q, "matvecs": st["matvecs"], "kernel_ms": st["kernel_ms"],
+                      "algorithmic_bytes": st["algorithmic_bytes"], "csr_lanes_per_row": lanes,
+                      "schedule_measurements": C.qsw_tune_measurements()}))
 
 
 def main():
     args = parse_args()
     if args.profile_steps:
-        run_profile_case(args.profile_steps)
+        run_profile_case(args)
         return
     if args.oracle_sample:
         print(json.dumps(oracle_sample()))

@@ -12,7 +12,9 @@ The paper precomputes the series {||L~^p||_1, p = 1..9} when a walk is built
   (A^p)^H, and no parallel-column tests.  Its starting block is
   [ones/n, x/n] with x_i = +-1 drawn from the counter-based SplitMix64
   generator (Steele, Lea & Flood 2014): output i is mix(seed + (i+1)*phi) with
-  phi = 0x9E3779B97F4A7C15 and x_i = -1 iff the top bit of that output is set.
+  phi = 0x9E3779B97F4A7C15 and x_i = -1 iff the top bit of that output is set;
+  for n = m^2 entry a + m b uses output min(a + m b, b + m a) (`start_signs`:
+  the column is a Hermitian m x m matrix).
   Ties in the row-norm sort are broken by ascending index.
 
 Pinned by tests/test_oracle_norms.py: exact powers against dense numpy powers,
@@ -51,6 +53,22 @@ def random_signs(n: int, seed: int = NORMEST_SEED) -> np.ndarray:
         z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
         z = z ^ (z >> np.uint64(31))
     return np.where((z >> np.uint64(63)) != 0, -1.0, 1.0)
+
+
+def start_signs(n: int, seed: int = NORMEST_SEED) -> np.ndarray:
+    """Second column of the starting block: +-1 signs from `random_signs`, drawn
+    symmetric under the transpose of a vectorised m x m matrix when n = m^2.
+    Entry r = a + m b takes the sign of index min(r, b + m a), so the column,
+    read as an m x m matrix, is real symmetric (Hermitian).  Higham & Tisseur
+    ask only for a random +-1 column; superoperators of the walks map
+    Hermitian matrices to Hermitian matrices, so this choice keeps every
+    iterate of the column Hermitian.  Other n: `random_signs` itself."""
+    x = random_signs(n, seed)
+    m = int(round(np.sqrt(n)))
+    if m * m != n:
+        return x
+    r = np.arange(n)
+    return x[np.minimum(r, (r // m) + m * (r % m))]
 
 
 def onenorm(A) -> float:
@@ -92,7 +110,7 @@ def onenorm_power_est(A, p: int, t: int = 2, itmax: int = 5, seed: int = NORMEST
     t = min(t, n)
     X = np.ones((n, t), dtype=np.complex128)
     if t > 1:
-        X[:, 1] = random_signs(n, seed)
+        X[:, 1] = start_signs(n, seed)
         for c in range(2, t):
             X[:, c] = random_signs(n, seed + c)
     X /= n

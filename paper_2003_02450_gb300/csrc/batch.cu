@@ -348,8 +348,9 @@ batch_norms_kernel(BArgs a) {
         // X = [1, +-1] / n
         for (long long r = ct; r < n; r += cstride) {
           X[r] = make_double2(1.0 / n, 0.0);
-          if (t > 1) {
-            const bool neg = (splitmix64(kSeed, (unsigned long long)r) >> 63) != 0;
+          if (t > 1) {   // signs symmetric under the transposed index (a Hermitian column)
+            const long long rt = (r / Nt) + (long long)Nt * (r % Nt);
+            const bool neg = (splitmix64(kSeed, (unsigned long long)(rt < r ? rt : r)) >> 63) != 0;
             X[n + r] = make_double2(neg ? -1.0 / n : 1.0 / n, 0.0);
           }
         }

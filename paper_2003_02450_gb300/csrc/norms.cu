@@ -30,10 +30,11 @@
 //   * on graphs where that box stays small (lattices), the adjoint step takes
 //     (A^H)^p sign(Y) = (A^H)^p 1 + (A^H)^p (sign(Y) - 1): the first term is one
 //     chain shared by every estimate, the second is supported on the box of Y;
-//   * L~ and L~^H map X^dag to (L X)^dag: the first column of the starting
-//     block (all ones) is Hermitian, so its products are taken on the upper
-//     triangle and mirrored, and a unit-vector pair e_(a,b), e_(b,a) (the row
-//     ranking ties them) costs one column, the other being its mirror.
+//   * L~ and L~^H map X^dag to (L X)^dag: both columns of the starting block
+//     (all ones, and random signs drawn symmetric under the transpose of the
+//     density-matrix index) are Hermitian, so their products are taken on the
+//     upper triangle and mirrored, and a unit-vector pair e_(a,b), e_(b,a) (the
+//     row ranking ties them) costs one column, the other being its mirror.
 // The last two change the rounding of some products, not their values.
 #include <math.h>
 #include <stddef.h>
@@ -265,13 +266,17 @@ __global__ void argmax_final_kernel(int nparts, const double* __restrict__ pv,
   }
 }
 
-__global__ void init_block_kernel(int n, int t, double2* __restrict__ X) {
+// X = [1, x] / n; x_r = +-1 from SplitMix64 output min(r, r^T), r^T the index
+// of the transposed density-matrix entry, so that x is a Hermitian (real
+// symmetric) N~ x N~ matrix like the first column.
+__global__ void init_block_kernel(int n, int Nt, int t, double2* __restrict__ X) {
   const double inv = 1.0 / n;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
        r += (long long)gridDim.x * blockDim.x) {
     X[r] = make_double2(inv, 0.0);
     if (t > 1) {
-      const bool neg = (splitmix64(kSeed, (unsigned long long)r) >> 63) != 0;
+      const long long rt = (r / Nt) + (long long)Nt * (r % Nt);
+      const bool neg = (splitmix64(kSeed, (unsigned long long)(rt < r ? rt : r)) >> 63) != 0;
       X[n + r] = make_double2(neg ? -inv : inv, 0.0);
     }
   }
@@ -591,10 +596,11 @@ struct Estimator {
   void sync() { QSW_CUDA_TRY(cudaStreamSynchronize(st)); }
 
   // out = M^p in (M = L or L^H) for `cols` columns, ping-ponging through tmp.
-  // herm0: column 0 is Hermitian (matrix-free operators: upper-triangle products).
+  // herm_cols: the first herm_cols columns are Hermitian (matrix-free operators:
+  // upper-triangle products).
   void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols,
-            bool herm0 = false) {
-    if (herm0 && (box_ok || op->gq.active)) {
+            int herm_cols = 0) {
+    if (herm_cols > 0 && (box_ok || op->gq.active)) {
       const unsigned grid = (unsigned)std::min(Nt, 152 * 8);
       const double2* src = in;
       for (int k = 0; k < p; ++k) {
@@ -612,7 +618,7 @@ struct Estimator {
         src = dst;
       }
       QSW_CUDA_TRY(cudaGetLastError());
-      if (cols > 1) mult(adjoint, p, in + n, out_ + n, tmp ? tmp + n : nullptr, cols - 1);
+      if (cols > 1) mult(adjoint, p, in + n, out_ + n, tmp ? tmp + n : nullptr, cols - 1, herm_cols - 1);
       return;
     }
     const double2* src = in;
@@ -753,7 +759,7 @@ struct Estimator {
     }
     for (; ones_pow < p; ++ones_pow)   // Hermitian: upper-triangle products
       mult(true, 1, ones.as<double2>() + nn * ones_pow, ones.as<double2>() + nn * (ones_pow + 1),
-           nullptr, 1, true);
+           nullptr, 1, 1);
   }
 
   // Y(:, c) <- (A^H)^p sign(Y(:, c)) = (A^H)^p 1 + (A^H)^p D_c, D_c = sign(Y(:, c)) - 1
@@ -827,15 +833,17 @@ struct Estimator {
     const size_t blk = (size_t)n * t;
     chain.alloc(sizeof(double2) * blk);
     chain_tmp.alloc(sizeof(double2) * blk);
-    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, chain.as<double2>());
+    QSW_LAUNCH init_block_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, Nt, t,
+                                                                          chain.as<double2>());
     QSW_CUDA_TRY(cudaGetLastError());
     chain_pow = 0;
   }
   const double2* chain_power(int p) {
     QSW_CHECK_ARG(chain_pow >= 0 && chain_pow <= p, QSW_ERR_CUDA, "estimator chain out of order");
-    // column 0 (all ones / n) is Hermitian, and so are its powers
+    // both columns (all ones, and the transpose-symmetric signs) are
+    // Hermitian, and so are their powers
     for (; chain_pow < p; ++chain_pow) {
-      mult(false, 1, chain.as<double2>(), chain_tmp.as<double2>(), nullptr, t, true);
+      mult(false, 1, chain.as<double2>(), chain_tmp.as<double2>(), nullptr, t, t);
       std::swap(chain, chain_tmp);
     }
     return chain.as<double2>();
@@ -889,7 +897,7 @@ struct Estimator {
       } else {
         QSW_LAUNCH sign_kernel<<<grid_for((long long)n * tz, 256, 4096), 256, 0, st>>>(
             (long long)n * tz, Yp, Xp);
-        mult(true, p, Xp, Yp, Wp, tz, k == 1);   // k = 1: sign(Y(:, 0)) is Hermitian
+        mult(true, p, Xp, Yp, Wp, tz, k == 1 ? tz : 0);   // k = 1: sign(Y) is Hermitian
       }
       if (mirror) mirror_column();
       QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());

@@ -66,7 +66,7 @@ def _achievable(L, pmax=9):
     L^p [1, s] / n (the values the estimator can return)."""
     n = L.shape[0]
     X0 = np.ones((n, 2), complex)
-    X0[:, 1] = normest.random_signs(n)
+    X0[:, 1] = normest.start_signs(n)
     X0 /= n
     P = np.eye(n, dtype=complex)
     out = {}

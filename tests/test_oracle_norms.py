@@ -189,3 +189,30 @@ def test_iteration_cap():
     assert [r["k"] for r in tr] == [1, 2] and tr[1]["stop"] == "itmax"
     est, tr = _trace(A_ADJ, 1, itmax=0)   # stops after the starting block
     assert est == 1.0 and tr[0]["stop"] == "itmax"
+
+
+def test_start_signs_symmetric_under_transpose():
+    # n = m^2: the column read as an m x m matrix (column-major) is symmetric,
+    # its entries are the SplitMix64 signs of the canonical index, and it is
+    # not constant (both signs occur); other n keep the plain stream.
+    for m in (2, 5, 16):
+        x = normest.start_signs(m * m)
+        X = x.reshape((m, m), order="F")
+        assert np.array_equal(X, X.T)
+        raw = normest.random_signs(m * m)
+        for a in range(m):
+            for b in range(m):
+                assert X[a, b] == raw[min(a + m * b, b + m * a)]
+    assert set(normest.start_signs(256).tolist()) == {-1.0, 1.0}
+    assert np.array_equal(normest.start_signs(40), normest.random_signs(40))
+
+
+def test_estimate_unchanged_in_exact_arithmetic_terms_for_superoperator():
+    # the estimator with the Hermitian starting column still returns a
+    # reachable lower bound of ||L~^p||_1 on a walk's superoperator
+    g = W.random_digraph(6, 0.4, 3)
+    L = superop.superoperator(graph.lqsw_walk(graph.adjacency(g)), 0.4)
+    for p in (2, 3, 5):
+        ex = normest.onenorm_power_exact(L, p)
+        est = normest.onenorm_power_est(L, p)
+        assert ex / 10 <= est <= ex * (1 + 1e-12)
