@@ -30,6 +30,8 @@
 #include <algorithm>
 #include <mutex>
 #include <numeric>
+#include <thread>
+#include <chrono>
 #include <type_traits>
 
 #include "matfree.cuh"
@@ -86,6 +88,7 @@ struct BWalk {
   Job* jobs;
   int njobs;
   long long* counters; // [0] matvecs, [1] fupdates, [2] plan mismatch
+  int* done;           // host-mapped completion flag, or null
 };
 
 struct BArgs {
@@ -771,6 +774,12 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
   if (crank == 0 && threadIdx.x == 0) {
     W.counters[0] = matvecs;
     W.counters[1] = fupd;
+    // every CTA of the group is past the sync that ended the last job: the
+    // walk's populations are final; tell a host that hands walks out early
+    if (W.done) {
+      __threadfence_system();
+      *(volatile int*)W.done = 1;
+    }
   }
 }
 
@@ -899,7 +908,7 @@ void allow_small_smem(int device) {
 
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,
-               qsw_batch_stats* stats) {
+               qsw_batch_stats* stats, const WalkSink* sink) {
   cudaStream_t st = ctx->stream;
   QSW_CHECK_ARG(n0 >= 1 && n0 <= kMaxRhs, QSW_ERR_INVALID_ARG, "n0 must be 1..4");
   std::vector<BWalk> hw(count);
@@ -949,6 +958,7 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     W.norm_span = std::max(t0s[w], steps[w] * dts[w]);
     W.dp = dpbuf.as<double>() + (kNormPowers + 1) * w;
     W.counters = cnt.as<long long>() + 4 * w;
+    W.done = sink ? sink->d_done + w : nullptr;
     bufs.emplace_back();
     bufs.back().alloc(sizeof(double2) * 6 * op.n + sizeof(double) * op.n);
     W.est = bufs.back().as<double2>();
@@ -1069,6 +1079,21 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   }
   if (join) QSW_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
   QSW_CUDA_TRY(cudaEventRecord(e2, st));
+  if (sink) {
+    // hand finished walks out while the kernels run; the loop ends when both
+    // kernels have (their waits are cluster barriers, which always complete)
+    std::vector<char> seen(count, 0);
+    for (;;) {
+      const bool done = cudaEventQuery(e2) != cudaErrorNotReady;
+      for (int w = 0; w < count; ++w)
+        if (!seen[w] && ((volatile int*)sink->h_done)[w]) {
+          seen[w] = 1;
+          sink->ready(w);
+        }
+      if (done) break;
+      std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+  }
   std::vector<long long> hc(4 * count);
   QSW_CUDA_TRY(cudaMemcpyAsync(hc.data(), cnt.p, cnt.bytes, cudaMemcpyDeviceToHost, st));
   QSW_CUDA_TRY(cudaStreamSynchronize(st));

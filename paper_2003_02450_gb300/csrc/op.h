@@ -167,9 +167,18 @@ int tuned_csr_tpr(Op& op);       // autotuned lanes per row (cached per device a
 long long tune_measurements();   // schedule measurements made in this process
 void tune_reset();               // forget every tuned schedule
 // batch.cu
+// Receiver of walks as they finish inside one batched call: the kernel that
+// runs walk w stores 1 into the host-mapped int h_done[w] (device address
+// d_done + w, zero on entry) once the walk's populations are final, and
+// run_batch calls ready(w) while it waits for the kernels.
+struct WalkSink {
+  int* h_done;
+  int* d_done;
+  std::function<void(int)> ready;
+};
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,
-               qsw_batch_stats* stats);
+               qsw_batch_stats* stats, const WalkSink* sink = nullptr);
 // est.cu
 void run_survival(Op& op, const double* d_rho0, double t_end, int q, int sink, double* eta,
                   double* d_pops, qsw_series_stats* stats);

@@ -5,12 +5,16 @@
 // A free worker takes every queued request that fits the device-memory budget
 // (first come, first served, up to max_batch), builds their superoperators on
 // its stream, uploads their initial states, and runs them as ONE batched launch
-// (batch.cu: a thread-block cluster per walk); the populations come back to
-// pinned host memory and the requests complete.  While one worker's batch is on
-// the GPU, requests that arrive are taken by another worker and launched on its
-// stream, so their work overlaps on the device (continuous batching at launch
-// granularity).  Memory is released in stream order, so no worker ever
-// synchronises the whole device.
+// (batch.cu: a thread-block cluster per walk).  A walk's cluster raises a
+// host-mapped flag when the walk's populations are final; the worker polls the
+// flags while the launch runs, copies each finished walk's populations to the
+// caller on its copy stream and completes that request at once, so a short
+// walk does not wait for the longest walk of its batch.  While one worker's
+// batch is on the GPU, requests that arrive are taken by another worker and
+// launched on its stream, so their work overlaps on the device (continuous
+// batching at launch granularity, completion at walk granularity).  A batch's
+// device memory is released in stream order when its launch ends (and only then
+// counted free for admission), so no worker ever synchronises the whole device.
 //
 // A walk's result does not depend on the other walks of its batch: each walk
 // is computed by its own cluster with its own reductions in a fixed order, so a
@@ -90,10 +94,27 @@ struct qsw_server {
   std::vector<std::thread> threads;
   std::vector<qsw_ctx*> ctxs;
   std::vector<cudaStream_t> streams;
+  std::vector<cudaStream_t> copy_streams;  // per worker: early copies of finished walks
+  std::vector<int*> done_h;                // per worker: host-mapped completion flags
+  std::vector<int*> done_d;                //   (max_batch each) and their device addresses
   int64_t batches = 0;
+  int64_t early = 0;                       // requests completed before their batch ended
+
+  void complete(const std::shared_ptr<qsw::Req>& r, qsw::Clock::time_point t);
 
   void worker(int wi);
 };
+
+// Marks one request done (its populations are on the host) and wakes waiters.
+void qsw_server::complete(const std::shared_ptr<qsw::Req>& r, qsw::Clock::time_point t) {
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    if (r->done) return;
+    r->t_done = t;
+    r->done = 1;
+  }
+  cv_done.notify_all();
+}
 
 void qsw_server::worker(int wi) {
   using namespace qsw;
@@ -211,13 +232,41 @@ void qsw_server::worker(int wi) {
         bsteps.push_back(steps[k]);
       }
       if (!bops.empty()) {
-        qsw_batch_stats bs{};
-        st = qsw_batch_series(ctx, (int32_t)bops.size(), bops.data(), brho.data(), 1, bt0.data(),
-                              bdt.data(), bsteps.data(), bpops.data(), &bs);
+        // one batched launch; each walk's populations go to its caller as soon
+        // as its cluster (or CTA) has finished it, while the others still run
+        std::vector<std::shared_ptr<Req>> breqs;
+        for (size_t k = 0; k < live.size(); ++k)
+          if (live[k]->N < kWholeGpuVertices) breqs.push_back(live[k]);
+        for (size_t w = 0; w < bops.size(); ++w) done_h[wi][w] = 0;
+        cudaStream_t cs = copy_streams[wi];
+        WalkSink sink{done_h[wi], done_d[wi], [&](int w) {
+                        Req& r = *breqs[w];
+                        if (r.status != QSW_OK) return;
+                        if (cudaMemcpyAsync(r.pops_out, bpops[w],
+                                            sizeof(double) * (size_t)(r.steps + 1) * r.N,
+                                            cudaMemcpyDeviceToHost, cs) != cudaSuccess ||
+                            cudaStreamSynchronize(cs) != cudaSuccess)
+                          return;   // left to the copy after the launch
+                        complete(breqs[w], Clock::now());
+                        std::lock_guard<std::mutex> lk(mu);
+                        ++early;
+                      }};
+        try {
+          for (qsw_op* op : bops)
+            QSW_CHECK_ARG(reinterpret_cast<Op*>(op)->ctx == ctx, QSW_ERR_INVALID_ARG,
+                          "operator from another context");
+          qsw::run_batch(ctx, (int)bops.size(), reinterpret_cast<Op* const*>(bops.data()),
+                         brho.data(), 1, bt0.data(), bdt.data(), bsteps.data(), bpops.data(),
+                         nullptr, &sink);
+        } catch (const Error& e) {
+          st = e.status;
+          err = e.msg;
+        }
       }
-      if (st != QSW_OK) err = ctx->last_error;
+      if (st != QSW_OK && err.empty()) err = ctx->last_error;
       for (size_t k = 0; k < live.size() && st == QSW_OK; ++k) {
         Req& r = *live[k];
+        if (r.done) continue;   // handed out early
         if (cudaMemcpyAsync(r.pops_out, d_pops[k], sizeof(double) * (size_t)(r.steps + 1) * r.N,
                             cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess)
           st = QSW_ERR_CUDA;
@@ -231,13 +280,15 @@ void qsw_server::worker(int wi) {
     {
       std::lock_guard<std::mutex> lk(mu);
       for (auto& r : take) {
-        if (r->status == QSW_OK && st != QSW_OK) {
-          r->status = st;
-          r->error = err;
+        if (!r->done) {
+          if (r->status == QSW_OK && st != QSW_OK) {
+            r->status = st;
+            r->error = err;
+          }
+          r->t_done = t_done;
+          r->done = 1;
         }
-        r->t_done = t_done;
-        r->done = 1;
-        in_use -= r->footprint;
+        in_use -= r->footprint;   // the batch's device memory is released now
       }
     }
     cv_done.notify_all();
@@ -264,9 +315,19 @@ qsw_status qsw_server_create(int device, const qsw_server_config* cfg, qsw_serve
     s->budget = fr / 2;
   }
   for (int k = 0; k < s->workers; ++k) {
-    cudaStream_t st;
+    cudaStream_t st, cs;
     if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return QSW_ERR_CUDA;
     s->streams.push_back(st);
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return QSW_ERR_CUDA;
+    s->copy_streams.push_back(cs);
+    int* h = nullptr;
+    int* d = nullptr;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&h), sizeof(int) * s->max_batch, cudaHostAllocMapped) !=
+            cudaSuccess ||
+        cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0) != cudaSuccess)
+      return QSW_ERR_CUDA;
+    s->done_h.push_back(h);
+    s->done_d.push_back(d);
     qsw_ctx* c = nullptr;
     const qsw_status r = qsw_create(&c, device, st);
     if (r != QSW_OK) return r;
@@ -353,6 +414,8 @@ void qsw_server_destroy(qsw_server* s) {
   for (auto& t : s->threads) t.join();
   for (qsw_ctx* c : s->ctxs) qsw_destroy(c);
   for (cudaStream_t st : s->streams) cudaStreamDestroy(st);
+  for (cudaStream_t st : s->copy_streams) cudaStreamDestroy(st);
+  for (int* h : s->done_h) cudaFreeHost(h);
   delete s;
 }
 
