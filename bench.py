@@ -26,6 +26,7 @@ import sys
 import tempfile
 import time
 
+PROCESS_T0 = time.time()
 ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
@@ -41,6 +42,9 @@ def parse_args():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--warmup-seconds", type=float, default=0.0,
+                    help="default line: keep warming up until this many seconds after process "
+                         "start (in addition to --warmup steps)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -163,7 +167,14 @@ def cpu_baseline_block(sample: dict) -> dict:
 # ------------------------------------------------------------------ clocks --
 
 class ClockSampler:
-    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+    """nvidia-smi clocks and throttle reasons, sampled every 200 ms.
+
+    start() launches the sampler and waits until its first sample has arrived,
+    so that nvidia-smi's own start-up (driver queries that can hold up the
+    CUDA calls of the process being measured) is over before the caller's
+    work; mark() records the start of the timed region, and stop() keeps only
+    the samples taken after it."""
+    FIELDS = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
@@ -171,8 +182,9 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.path = None
+        self.t_mark = None
 
-    def start(self):
+    def start(self, settle_s: float = 5.0):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
@@ -182,6 +194,15 @@ class ClockSampler:
                 stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t_end = time.time() + settle_s
+        while time.time() < t_end and self.proc.poll() is None:
+            if os.path.getsize(self.path) > 0:
+                break
+            time.sleep(0.05)
+
+    def mark(self):
+        self.t_mark = time.time()
 
     def stop(self) -> dict:
         if self.proc is None:
@@ -192,18 +213,26 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        import datetime
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
+            if self.t_mark is not None:
+                try:
+                    ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                    if ts < self.t_mark - 0.2:
+                        continue
+                except ValueError:
+                    pass
             try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
+                sm.append(float(parts[2]))
+                smax.append(float(parts[3]))
             except ValueError:
                 continue
-            for name, v in zip(names, parts[5:9]):
+            for name, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(name)
         os.unlink(self.path)
@@ -349,23 +378,32 @@ def run_ours(args):
         st["nnz"] = info["nnz"]
         return st
 
-    for _ in range(args.warmup):
+    # the clock sampler starts before the warm-up: its start-up is over before
+    # the timed region, whose samples alone are kept
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    warm = 0
+    while warm < args.warmup or time.time() - PROCESS_T0 < args.warmup_seconds:
         one_step()
+        warm += 1
     torch.cuda.synchronize(dev)
     barrier()
     torch.cuda.synchronize(dev)
-    sampler = ClockSampler(local_rank)
-    sampler.start()
+    sampler.mark()
     l0 = C.qsw_kernel_launches()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    # L2 (129 MB) is flushed between timed steps by writing 256 MB
+    # L2 (129 MB) is flushed between timed steps by a 256 MB device-to-device
+    # copy (the copy engine, cudaMemcpyAsync): a fill kernel of the framework
+    # measured ~28 ms per call in the first process on a fresh box
+    flush_src = torch.zeros(256 << 20, dtype=torch.uint8, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    flush.copy_(flush_src)
     ev0.record(stream)
     stats = []
     for k in range(args.steps):
         if k:
-            flush.fill_(k & 0xFF)
+            flush.copy_(flush_src)
         stats.append(one_step())
     ev1.record(stream)
     torch.cuda.synchronize(dev)
@@ -453,7 +491,8 @@ def run_ours(args):
                        "omega": cfg.omega, "rho0": "uniform superposition (dense)",
                        "t0": cfg.t0, "dt": cfg.dt, "series_steps": q, "rows": n, "nnz": s0["nnz"],
                        "parallelism": f"replicas x{world} (one walk per GPU)",
-                       "l2": "flushed between timed steps (256 MB write); each step also writes its 51 output states (816 MB)"},
+                       "l2": "flushed between timed steps (256 MB device-to-device copy); each step also writes its 51 output states (816 MB)",
+                       "warmup_steps_run": warm, "warmup_until_s_after_start": args.warmup_seconds},
             "roofline": {"bound": "alu", "pipe": "fp64",
                          "kernel": f"series_kernel ({args.operator} operator, fused Taylor update)",
                          "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
@@ -539,6 +578,7 @@ def run_gqsw_workload(args):
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.mark()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = C.qsw_kernel_launches()
     e0.record(stream)
@@ -615,6 +655,7 @@ def run_nm_workload(args):
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.mark()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = C.qsw_kernel_launches()
     e0.record(stream)
@@ -688,6 +729,7 @@ def run_est_workload(args):
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.mark()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = C.qsw_kernel_launches()
     ev0.record(stream)
@@ -809,6 +851,7 @@ def run_batch_workload(args):
     torch.cuda.synchronize(dev)
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.mark()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     l0 = C.qsw_kernel_launches()
     ev0.record(stream)
@@ -998,6 +1041,7 @@ def run_grid_workload(args):
     peak_gbs, peak_kind = measured_peak_gbs()
     sampler = ClockSampler(0)
     sampler.start()
+    sampler.mark()
     for prec in ("c64", "c128"):
         cfg = W.grid45(prec)
         rho0 = torch.from_numpy(W.vec(cfg.rho0)).to(dev)
