@@ -1052,7 +1052,7 @@ def run_grid_workload(args):
                                            operator=args.operator)
             st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, cfg.steps, None, pops)
             info = C.qsw_op_info(ctx, op)
-            st["lanes_per_row"] = C.qsw_op_schedule(op)
+            st["lanes_per_row"], st["unroll"] = C.qsw_op_schedule(op, with_unroll=True)
             C.qsw_op_destroy(op)
             st["nnz"] = info["nnz"]
             return st
@@ -1082,6 +1082,7 @@ def run_grid_workload(args):
                                   "algorithmic_bytes_per_launch": s0["algorithmic_bytes"],
                                   "bytes_per_term_spmv": s0["bytes_per_matvec"]},
                      "csr_lanes_per_row": s0["lanes_per_row"] or None,
+                     "csr_unroll": s0["unroll"] or None,
                      "csr_equivalent": csr_equivalent(s0["nnz"], 2025 ** 2, peak_gbs, kms,
                                                       s0["matvecs"])}
         final_pops[prec] = pops.cpu().numpy()
@@ -1145,12 +1146,13 @@ def run_profile_case(args):
     op = C.qsw_build_superoperator(ctx, cfg.graph, None, cfg.omega, precision=prec,
                                    operator=args.operator, fixed_schedule=args.profile_fixed)
     st = C.qsw_expmv_series(ctx, op, rho0, cfg.t0, cfg.dt, q, out, None)
-    lanes = C.qsw_op_schedule(op)
+    lanes, unroll = C.qsw_op_schedule(op, with_unroll=True)
     C.qsw_op_destroy(op)
     C.qsw_destroy(ctx)
     print(json.dumps({"profile_case": cfg.name, "precision": prec, "operator": args.operator,
                       "series_steps": q, "matvecs": st["matvecs"], "kernel_ms": st["kernel_ms"],
                       "algorithmic_bytes": st["algorithmic_bytes"], "csr_lanes_per_row": lanes,
+                      "csr_unroll": unroll,
                       "schedule_measurements": C.qsw_tune_measurements()}))
 
 

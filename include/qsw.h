@@ -495,11 +495,12 @@ int64_t qsw_device_allocations(void);
  * Not in the paper (a schedule choice of this library).  The CSR sweep of
  * the series kernel runs TPR lanes per row of L~ (1, 2, 4, 8, 16 or 32), which
  * sets the cost of its shuffle reductions and how the operator stream is
- * coalesced.  The first qsw_expmv_series on a QSW_OPERATOR_CSR operator
+ * coalesced, and keeps 2 or 4 entries per lane in flight (unroll depth).
+ * The first qsw_expmv_series on a QSW_OPERATOR_CSR operator
  * (without QSW_BUILD_FIXED_SCHEDULE) looks up the device's choice for its
  * (precision, row-length bucket, size bucket); when there is none it times
- * every candidate with the series kernel on that operator (eight Taylor terms
- * from a fixed vector, about 20 short launches, plus two Taylor-term vectors
+ * every candidate pair with the series kernel on that operator (eight Taylor
+ * terms from a fixed vector, 36 short launches, plus two Taylor-term vectors
  * of workspace), keeps the fastest for the life of the process and uses it
  * for every later operator in that bucket.  Results depend on the choice
  * only through the summation order within a row (well inside the 1e-10
@@ -512,9 +513,11 @@ int64_t qsw_tune_measurements(void);
 /* Forget every tuned schedule (the next CSR operator of each bucket is
  * measured again).  Pure host call; not safe against concurrent series. */
 void qsw_tune_reset(void);
-/* The operator's CSR lanes per row (0 for a matrix-free operator): the
- * heuristic value until its first series, the tuned value after it. */
-qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row);
+/* The operator's CSR schedule (0 and 0 for a matrix-free operator): lanes
+ * per row and the row loop's unroll depth (2 or 4 entries per lane in flight;
+ * csr_unroll may be NULL).  The heuristic values until its first series, the
+ * tuned values after it. */
+qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row, int32_t* csr_unroll);
 
 /* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
  * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor

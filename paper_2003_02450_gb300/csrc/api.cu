@@ -706,10 +706,12 @@ int64_t qsw_tune_measurements(void) { return qsw::tune_measurements(); }
 
 void qsw_tune_reset(void) { qsw::tune_reset(); }
 
-qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row) {
+qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row, int32_t* csr_unroll) {
   if (!op || !csr_lanes_per_row) return QSW_ERR_INVALID_ARG;
   const Op* o = reinterpret_cast<const Op*>(op);
-  *csr_lanes_per_row = o->opkind == QSW_OPERATOR_CSR ? o->tpr : 0;
+  const bool csr = o->opkind == QSW_OPERATOR_CSR;
+  *csr_lanes_per_row = csr ? o->tpr : 0;
+  if (csr_unroll) *csr_unroll = csr ? o->csr_unroll : 0;
   return QSW_OK;
 }
 

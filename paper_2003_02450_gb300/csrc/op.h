@@ -111,7 +111,8 @@ struct Op {
   double dp[kNormPowers + 1] = {0};  // dp[0] = ||L||_1, dp[p-1] = ||L^p||^(1/p)
   DevBuf dp_dev;
   int tpr = 8;     // SpMV threads per row
-  bool tpr_fixed = false;   // set: keep tpr (tuned, or QSW_BUILD_FIXED_SCHEDULE)
+  int csr_unroll = 2;       // CSR sweep: entries per lane in flight (2 or 4)
+  bool tpr_fixed = false;   // set: keep tpr and csr_unroll (tuned, or QSW_BUILD_FIXED_SCHEDULE)
   bool norms_ready = false;
 
   // series workspace
@@ -163,7 +164,7 @@ template <class R> struct MfOp;
 template <class R> MfOp<R> make_mf(const Op& op, bool adjoint);
 void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
 int choose_tpr(double avg_row);
-int tuned_csr_tpr(Op& op);       // autotuned lanes per row (cached per device and bucket)
+void tune_csr_schedule(Op& op);  // autotuned lanes per row and unroll (cached per bucket)
 long long tune_measurements();   // schedule measurements made in this process
 void tune_reset();               // forget every tuned schedule
 // batch.cu

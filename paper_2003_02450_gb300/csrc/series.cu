@@ -246,7 +246,9 @@ template <class VT> struct Epilogue {
   }
 };
 
-template <class VT, int OPK, int TPR>
+// UNR: entries per lane in flight in the CSR sweep's row loop (2 or 4; the
+// matrix-free and global sweeps ignore it).
+template <class VT, int OPK, int TPR, int UNR = 2>
 __global__ void __launch_bounds__(kBlock, 4)
 series_kernel(SeriesArgs a) {
   using R = typename Cplx<VT>::R;
@@ -448,6 +450,33 @@ series_kernel(SeriesArgs a) {
             const int e1 = valid ? rowptr[r + 1] : 0;
             R ax = 0, ay = 0;
             int e = e0 + glane;
+            if (UNR == 4) {   // four entries in flight, two accumulator pairs
+              R bx = 0, by = 0;
+              for (; e + 3 * TPR < e1; e += 4 * TPR) {
+                const int c0 = __ldcs(col + e);
+                const int c1 = __ldcs(col + e + TPR);
+                const int c2 = __ldcs(col + e + 2 * TPR);
+                const int c3 = __ldcs(col + e + 3 * TPR);
+                const VT v0 = __ldcs(val + e);
+                const VT v1 = __ldcs(val + e + TPR);
+                const VT v2 = __ldcs(val + e + 2 * TPR);
+                const VT v3 = __ldcs(val + e + 3 * TPR);
+                const VT x0 = __ldcg(kcur + c0);
+                const VT x1 = __ldcg(kcur + c1);
+                const VT x2 = __ldcg(kcur + c2);
+                const VT x3 = __ldcg(kcur + c3);
+                ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+                ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+                bx = fma(v1.x, x1.x, fma(-v1.y, x1.y, bx));
+                by = fma(v1.x, x1.y, fma(v1.y, x1.x, by));
+                ax = fma(v2.x, x2.x, fma(-v2.y, x2.y, ax));
+                ay = fma(v2.x, x2.y, fma(v2.y, x2.x, ay));
+                bx = fma(v3.x, x3.x, fma(-v3.y, x3.y, bx));
+                by = fma(v3.x, x3.y, fma(v3.y, x3.x, by));
+              }
+              ax += bx;
+              ay += by;
+            }
             for (; e + TPR < e1; e += 2 * TPR) {
               const int c0 = __ldcs(col + e);
               const int c1 = __ldcs(col + e + TPR);
@@ -710,11 +739,11 @@ __global__ void diag_state_kernel(int nt, long long n, const double* __restrict_
   }
 }
 
-template <class VT, int OPK, int TPR>
+template <class VT, int OPK, int TPR, int UNR = 2>
 cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* grid_out) {
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-      &per_sm, series_kernel<VT, OPK, TPR>, kBlock, 0);
+      &per_sm, series_kernel<VT, OPK, TPR, UNR>, kBlock, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const long long want =
@@ -726,27 +755,34 @@ cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* gr
   SeriesArgs args = a;
   void* params[] = {&args};
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  return cudaLaunchCooperativeKernel((const void*)series_kernel<VT, OPK, TPR>, dim3(grid),
+  return cudaLaunchCooperativeKernel((const void*)series_kernel<VT, OPK, TPR, UNR>, dim3(grid),
                                      dim3(kBlock), params, 0, st);
 }
 
 template <class VT>
-cudaError_t launch_series_op(const Op& op, int tpr, bool herm, const SeriesArgs& a, int sms,
-                             cudaStream_t st, int* g) {
+cudaError_t launch_series_op(const Op& op, int tpr, int unr, bool herm, const SeriesArgs& a,
+                             int sms, cudaStream_t st, int* g) {
   if (op.gq.active)
     return herm ? launch_series<VT, kOpGlobalHerm, 1>(a, sms, st, g)
                 : launch_series<VT, kOpGlobal, 1>(a, sms, st, g);
   if (op.opkind == QSW_OPERATOR_MATRIX_FREE)
     return herm ? launch_series<VT, kOpMatfreeHerm, 1>(a, sms, st, g)
                 : launch_series<VT, kOpMatfree, 1>(a, sms, st, g);
+#define QSW_CSR_CASE(T)                                                        \
+  case T:                                                                      \
+    return unr == 4 ? launch_series<VT, kOpCsr, T, 4>(a, sms, st, g)           \
+                    : launch_series<VT, kOpCsr, T, 2>(a, sms, st, g);
   switch (tpr) {
-    case 1: return launch_series<VT, kOpCsr, 1>(a, sms, st, g);
-    case 2: return launch_series<VT, kOpCsr, 2>(a, sms, st, g);
-    case 4: return launch_series<VT, kOpCsr, 4>(a, sms, st, g);
-    case 8: return launch_series<VT, kOpCsr, 8>(a, sms, st, g);
-    case 16: return launch_series<VT, kOpCsr, 16>(a, sms, st, g);
-    default: return launch_series<VT, kOpCsr, 32>(a, sms, st, g);
+    QSW_CSR_CASE(1)
+    QSW_CSR_CASE(2)
+    QSW_CSR_CASE(4)
+    QSW_CSR_CASE(8)
+    QSW_CSR_CASE(16)
+    default:
+      return unr == 4 ? launch_series<VT, kOpCsr, 32, 4>(a, sms, st, g)
+                      : launch_series<VT, kOpCsr, 32, 2>(a, sms, st, g);
   }
+#undef QSW_CSR_CASE
 }
 
 }  // namespace
@@ -758,18 +794,20 @@ int choose_tpr(double avg_row) { return avg_row <= 96 ? 2 : 4; }
 
 // ------------------------------------------------ autotuned CSR lanes per row
 // The CSR sweep's lanes per row (TPR) set the cost of the shuffle reduction and
-// how the operator stream is coalesced; the best value depends on the row
-// lengths, the precision and the size, and on the part.  The first CSR series
+// how the operator stream is coalesced, its unroll depth (2 or 4 entries per
+// lane in flight) how many loads each lane keeps waiting; the best pair depends
+// on the row lengths, the precision and the size, and on the part.  The first CSR series
 // on a device for a (precision, row-length bucket, size bucket) times every
-// candidate with the series kernel itself on that operator (one job of
+// candidate pair with the series kernel itself on that operator (one job of
 // kTuneTerms Taylor terms from a fixed vector, tolerance 0 so that every
 // candidate runs the same terms, a warm-up launch then two timed launches) and
-// keeps the fastest for the life of the process.  Results depend on TPR only
-// through the summation order of each row.
+// keeps the fastest for the life of the process.  Results depend on the pair
+// only through the summation order of each row.
 namespace {
 
 constexpr int kTuneTerms = 8;
 constexpr int kTprCandidates[] = {1, 2, 4, 8, 16, 32};
+constexpr int kUnrollCandidates[] = {2, 4};
 
 struct TuneKey {
   int device, precision, row_bucket, n_bucket;
@@ -782,7 +820,7 @@ struct TuneKey {
 };
 
 std::mutex g_tune_mu;
-std::map<TuneKey, int> g_tune_tpr;
+std::map<TuneKey, std::pair<int, int>> g_tune_tpr;   // (lanes per row, unroll)
 std::atomic<long long> g_tune_measurements{0};
 
 __global__ void tune_fill_kernel(long long n, double2* __restrict__ x) {
@@ -806,12 +844,16 @@ void tune_reset() {
   g_tune_tpr.clear();
 }
 
-int tuned_csr_tpr(Op& op) {
+void tune_csr_schedule(Op& op) {
   const TuneKey key = csr_tune_key(op);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_tpr.find(key);
-    if (it != g_tune_tpr.end()) return it->second;
+    if (it != g_tune_tpr.end()) {
+      op.tpr = it->second.first;
+      op.csr_unroll = it->second.second;
+      return;
+    }
   }
   cudaStream_t st = op.ctx->stream;
   const bool f32 = op.precision == QSW_C64_BULK;
@@ -848,16 +890,17 @@ int tuned_csr_tpr(Op& op) {
   cudaEvent_t e0, e1;
   QSW_CUDA_TRY(cudaEventCreate(&e0));
   QSW_CUDA_TRY(cudaEventCreate(&e1));
-  int best = op.tpr;
+  std::pair<int, int> best{op.tpr, op.csr_unroll};
   float best_ms = 0.f;
-  for (int tpr : kTprCandidates) {
+  for (int tpr : kTprCandidates)
+  for (int unr : kUnrollCandidates) {
     float tmin = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
       QSW_CUDA_TRY(cudaMemsetAsync(ctrl.p, 0, sizeof(Ctrl), st));
       QSW_CUDA_TRY(cudaEventRecord(e0, st));
       int grid = 0;
-      QSW_CUDA_TRY(f32 ? launch_series_op<float2>(op, tpr, false, a, op.ctx->num_sms, st, &grid)
-                       : launch_series_op<double2>(op, tpr, false, a, op.ctx->num_sms, st, &grid));
+      QSW_CUDA_TRY(f32 ? launch_series_op<float2>(op, tpr, unr, false, a, op.ctx->num_sms, st, &grid)
+                       : launch_series_op<double2>(op, tpr, unr, false, a, op.ctx->num_sms, st, &grid));
       QSW_CUDA_TRY(cudaEventRecord(e1, st));
       QSW_CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -871,14 +914,16 @@ int tuned_csr_tpr(Op& op) {
       throw Error{QSW_ERR_NOT_CONVERGED, "CSR schedule tuning: grid barrier wait exceeded its limit"};
     if (best_ms == 0.f || tmin < best_ms) {
       best_ms = tmin;
-      best = tpr;
+      best = {tpr, unr};
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   g_tune_measurements.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lock(g_tune_mu);
-  return g_tune_tpr.emplace(key, best).first->second;   // a concurrent tuner may have won
+  const auto chosen = g_tune_tpr.emplace(key, best).first->second;   // a concurrent tuner may have won
+  op.tpr = chosen.first;
+  op.csr_unroll = chosen.second;
 }
 
 void upload_theta_batch();
@@ -1004,7 +1049,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   const bool f32 = op.precision == QSW_C64_BULK;
   const size_t vbytes = f32 ? sizeof(float2) : sizeof(double2);
   if (op.opkind == QSW_OPERATOR_CSR && !op.tpr_fixed) {   // first CSR series: tuned schedule
-    op.tpr = tuned_csr_tpr(op);
+    tune_csr_schedule(op);
     op.tpr_fixed = true;
   }
   op.kbuf.alloc(2 * vbytes * (size_t)op.n);
@@ -1070,8 +1115,8 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   QSW_CUDA_TRY(cudaEventCreate(&ev1));
   QSW_CUDA_TRY(cudaEventRecord(ev0, st));
   int grid = 0;
-  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid)
-                      : launch_series_op<double2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid);
+  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
   QSW_CUDA_TRY(e);
   QSW_CUDA_TRY(cudaEventRecord(ev1, st));
   Ctrl h{};
@@ -1217,8 +1262,8 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
   a.tol = tolerance(op.precision);
 
   int grid = 0;
-  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid)
-                      : launch_series_op<double2>(op, op.tpr, herm, a, op.ctx->num_sms, st, &grid);
+  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
   QSW_CUDA_TRY(e);
   Ctrl h{};
   QSW_CUDA_TRY(cudaMemcpyAsync(&h, ctrl, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));

@@ -137,7 +137,7 @@ _SIGNATURES = {
     "qsw_device_allocations": ([], c_int64),
     "qsw_tune_measurements": ([], c_int64),
     "qsw_tune_reset": ([], None),
-    "qsw_op_schedule": ([c_void_p, POINTER(c_int32)], c_int32),
+    "qsw_op_schedule": ([c_void_p, POINTER(c_int32), POINTER(c_int32)], c_int32),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
     "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
     "qsw_server_wait": ([c_void_p, c_int64, c_double, POINTER(qsw_request_result)], c_int32),
@@ -497,10 +497,11 @@ def qsw_tune_reset() -> None:
     lib().qsw_tune_reset()
 
 
-def qsw_op_schedule(op) -> int:
-    v = c_int32()
-    _check(lib().qsw_op_schedule(op, byref(v)))
-    return v.value
+def qsw_op_schedule(op, with_unroll: bool = False):
+    """CSR lanes per row (0 for matrix-free); with_unroll: (lanes, unroll depth)."""
+    v, u = c_int32(), c_int32()
+    _check(lib().qsw_op_schedule(op, byref(v), byref(u)))
+    return (v.value, u.value) if with_unroll else v.value
 
 
 def qsw_theta_table(precision="c128") -> np.ndarray:

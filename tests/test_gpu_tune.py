@@ -1,4 +1,5 @@
-"""The autotuned CSR schedule (lanes per row of the series kernel's CSR sweep).
+"""The autotuned CSR schedule (lanes per row and unroll depth of the series
+kernel's CSR sweep).
 
 The first CSR series of a (precision, row-length, size) bucket measures every
 candidate and caches the fastest; later operators of the bucket reuse it.  The
@@ -43,14 +44,16 @@ def test_tuned_csr_schedule_is_cached_and_exact(ctx, precision):
     op = C.qsw_build_superoperator(ctx.handle, g, None, 0.35, precision=precision, operator="csr")
     heuristic = C.qsw_op_schedule(op)
     assert heuristic in (1, 2, 4, 8, 16, 32)
+    assert C.qsw_op_schedule(op, with_unroll=True) == (heuristic, 2)
     got = _series(ctx, op, g, rho0, 12, 0.25)
     tuned = C.qsw_op_schedule(op)
     assert tuned in (1, 2, 4, 8, 16, 32)
+    assert C.qsw_op_schedule(op, with_unroll=True)[1] in (2, 4)
     assert C.qsw_tune_measurements() == m0 + 1           # one measurement for the bucket
     # a second operator of the same bucket reuses the choice without measuring
     op2 = C.qsw_build_superoperator(ctx.handle, g, None, 0.6, precision=precision, operator="csr")
     _series(ctx, op2, g, rho0, 3, 0.25)
-    assert C.qsw_op_schedule(op2) == tuned
+    assert C.qsw_op_schedule(op2, with_unroll=True) == C.qsw_op_schedule(op, with_unroll=True)
     assert C.qsw_tune_measurements() == m0 + 1
     # set_omega keeps the tuned schedule (same structure)
     C.qsw_set_omega(ctx.handle, op2, 0.2)
@@ -59,7 +62,7 @@ def test_tuned_csr_schedule_is_cached_and_exact(ctx, precision):
     opf = C.qsw_build_superoperator(ctx.handle, g, None, 0.35, precision=precision, operator="csr",
                                     fixed_schedule=True)
     ref_fixed = _series(ctx, opf, g, rho0, 12, 0.25)
-    assert C.qsw_op_schedule(opf) == heuristic
+    assert C.qsw_op_schedule(opf, with_unroll=True) == (heuristic, 2)
     assert C.qsw_tune_measurements() == m0 + 1
     walk = graph.lqsw_walk(graph.adjacency(g))
     L = superop.superoperator(walk, 0.35)
@@ -79,4 +82,5 @@ def test_matrix_free_operator_has_no_csr_schedule(ctx):
     from paper_2003_02450_gb300 import qsw as C
     op = C.qsw_build_superoperator(ctx.handle, W.cycle_graph(8), None, 0.5)
     assert C.qsw_op_schedule(op) == 0
+    assert C.qsw_op_schedule(op, with_unroll=True) == (0, 0)
     C.qsw_op_destroy(op)
