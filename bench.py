@@ -922,6 +922,15 @@ def run_batch_workload(args):
                        "steps": q, "dt": dt, "clusters": s0["clusters"]},
             "batch": {"norms_ms": s0["norms_ms"], "series_ms": s0["series_ms"],
                       "matvecs": s0["matvecs"], "fupdates": s0["fupdates"]},
+            "roofline": {
+                "bound": "latency (FP32 operator products + FP64 output sums, L2-resident terms)",
+                "kernel": "batch_series_kernel + batch_small_kernel (series phase)",
+                "achieved_tflops": s0["algorithmic_flops"] / (s0["series_ms"] * 1e-3) / 1e12,
+                "hbm_view_gbs": s0["algorithmic_bytes"] / (s0["series_ms"] * 1e-3) / 1e9,
+                "hbm_peak_gbs": measured_peak_gbs()[0],
+                "hbm_frac": s0["algorithmic_bytes"] / (s0["series_ms"] * 1e-3) / 1e9 / measured_peak_gbs()[0],
+                "algorithmic_flops_per_step": s0["algorithmic_flops"],
+                "algorithmic_bytes_per_step": s0["algorithmic_bytes"]},
             "single_walk_c128": {"ms": single_ms, "walks_per_s": len(walks) * 1000.0 / single_ms,
                                  "what": "per walk: build (incl. its 1-norm series) + one "
                                          "qsw_expmv_series per initial state"},

@@ -312,6 +312,13 @@ typedef struct {
   int32_t small_walks;  /* walks whose two n x n0 Taylor-term blocks fit in
                            64 KB: run by one thread block each with the terms
                            in shared memory, alongside the clusters */
+  double algorithmic_flops;  /* series phase, all walks: the operator's flops
+                                on every right-hand side (FP32 for complex64
+                                bulk walks, FP64 otherwise) plus the FP64 output
+                                updates, counted as in qsw_series_stats */
+  double algorithmic_bytes;  /* series phase, all walks: operator data, term
+                                read and written, output updates per
+                                application, as in qsw_series_stats */
 } qsw_batch_stats;
 
 /* Many independent walks in one launch (not in the paper): walk w is `ops[w]`

@@ -1114,9 +1114,27 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     stats->norms_ms = ms1;
     stats->series_ms = ms2;
     long long mv = 0, fu = 0;
-    for (int w = 0; w < count; ++w) { mv += hc[4 * w]; fu += hc[4 * w + 1]; }
+    double flops = 0.0, bytes = 0.0;
+    for (int w = 0; w < count; ++w) {
+      mv += hc[4 * w];
+      fu += hc[4 * w + 1];
+      // per walk, as for one series: the Hermitian form computes the upper
+      // triangle; every application acts on the walk's n0 right-hand sides
+      const Op& op = *ops[w];
+      const BWalk& W = hw[w];
+      const double frac = W.herm ? (op.Nt + 1.0) / (2.0 * op.Nt) : 1.0;
+      const double elems = frac * (double)op.n * n0;
+      const double offdiag = frac * (double)(op.nnz_csr - op.n - op.g.n_jumps) * n0;
+      const double per_app = 4.0 * offdiag + 13.0 * elems + 4.0 * op.g.n_jumps * n0;
+      const double vb = W.f32 ? sizeof(float2) : sizeof(double2);
+      flops += (double)hc[4 * w] * per_app + 7.0 * (elems / n0) * (double)hc[4 * w + 1] * n0;
+      bytes += (double)hc[4 * w] * (op_bytes(op) + 2.0 * elems * vb) +
+               32.0 * elems * (double)hc[4 * w + 1];
+    }
     stats->matvecs = mv;
     stats->fupdates = fu;
+    stats->algorithmic_flops = flops;
+    stats->algorithmic_bytes = bytes;
   }
 }
 

@@ -68,7 +68,8 @@ class qsw_zcsr(ctypes.Structure):
 class qsw_batch_stats(ctypes.Structure):
     _fields_ = [("walks", c_int32), ("clusters", c_int32), ("norms_ms", c_double),
                 ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64),
-                ("small_walks", c_int32)]
+                ("small_walks", c_int32), ("algorithmic_flops", c_double),
+                ("algorithmic_bytes", c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
