@@ -213,3 +213,47 @@ def test_server_mix_with_whole_gpu_walks_matches_oracle_and_alone():
             assert np.array_equal(alone.pops, r.pops), (g.n, prec)
     finally:
         C.qsw_server_destroy(srv)
+
+
+def test_server_completes_short_walks_of_a_batch_first():
+    """One batched launch holding one long walk (N = 120, 100 steps) and
+    several tiny ones (N = 6..10, 2 steps): each walk's result is handed out as
+    soon as its cluster has finished it, so the tiny walks complete (and their
+    latency is measured) well before the long one; results match the oracle."""
+    ensure_built()
+    from paper_2003_02450_gb300 import qsw as C
+    big_g = W.erdos_renyi_mean_degree(120, 8.0, 4242)
+    big = C.Request(big_g, 0.4, 0.0, 0.1, 100, "c128", populations=np.eye(120)[0])
+    small = []
+    for k in range(6):
+        n = 6 + k % 5
+        g = W.erdos_renyi_mean_degree(n, 3.0, 500 + k)
+        r = C.Request(g, 0.5, 0.0, 0.1, 2, "c128", populations=np.eye(n)[0])
+        r.meta = (g, n)
+        small.append(r)
+    # one worker, one batch: the long walk is submitted first, the tiny ones
+    # right behind it, so that the worker takes all of them into one launch
+    srv = C.qsw_server_create(0, workers=1, max_batch=16, memory_budget_bytes=4e9)
+    try:
+        # a whole-GPU walk (N >= 160 runs alone) keeps the only worker busy
+        # while the seven walks queue up behind it; the worker then takes all
+        # seven into one batched launch
+        blocker = C.Request(W.erdos_renyi_mean_degree(300, 8.0, 77), 0.3, 0.0, 0.1, 60, "c128",
+                            populations=np.eye(300)[0])
+        C.qsw_server_submit(srv, blocker)
+        for r in [big] + small:
+            C.qsw_server_submit(srv, r)
+        C.qsw_server_wait(srv, blocker, 300.0)
+        res_big = C.qsw_server_wait(srv, big, 300.0)
+        res_small = [C.qsw_server_wait(srv, r, 300.0) for r in small]
+        st = C.qsw_server_stats(srv)
+    finally:
+        C.qsw_server_destroy(srv)
+    assert st["batches"] == 2, st   # the blocker, then one launch holding all seven
+    assert max(x["latency_ms"] for x in res_small) < res_big["latency_ms"]
+    for r in small:
+        g, n = r.meta
+        ref = _oracle_pops(g, 0.5, W.basis_state(n, 0), 0.0, 2)
+        assert np.max(np.abs(r.pops - ref)) <= 1e-10
+    ref = _oracle_pops(big_g, 0.4, W.basis_state(120, 0), 0.0, 100)
+    assert np.max(np.abs(big.pops - ref)) <= 1e-10
