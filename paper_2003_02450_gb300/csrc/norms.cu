@@ -457,32 +457,41 @@ mf_box_kernel(MfOp<double> op, const int* __restrict__ list, const int* __restri
   }
 }
 
-// y = L~ x (or L~^H x) for a Hermitian x; both maps preserve Hermiticity, so
-// only the upper triangle is computed (the same per-element helpers and order
-// as the full product) and mirrored.  The diagonal's imaginary part, zero in
-// exact arithmetic, is stored as zero, which keeps y exactly Hermitian.  Blocks
-// take the columns longest first (column j holds j + 1 upper-triangle rows).
+// y_c = L~ x_c (or L~^H x_c) for `cols` Hermitian vectors stored n apart; both
+// maps preserve Hermiticity, so only the upper triangle is computed (the same
+// per-element helpers and order as the full product) and mirrored.  The
+// diagonal's imaginary part, zero in exact arithmetic, is stored as zero,
+// which keeps y exactly Hermitian.  Warps stride over the upper triangle's
+// 64-row windows (nearly equal work each); every window is applied to all
+// columns while its rows and neighbour lists are at hand.
 template <bool ADJ>
 __global__ void __launch_bounds__(kBoxBlock)
-mf_herm_kernel(MfOp<double> op, const double2* __restrict__ x, double2* __restrict__ y) {
+mf_herm_kernel(MfOp<double> op, int cols, long long n, const double2* __restrict__ x,
+               double2* __restrict__ y) {
   const int Nt = op.Nt;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int jb = blockIdx.x; jb < Nt; jb += gridDim.x) {
-    const int j = Nt - 1 - jb;
-    for (int i0 = warp * kItemRows; i0 <= j; i0 += kBoxWarps * kItemRows) {
-      int irow[2];
+  const int lane = threadIdx.x & 31;
+  const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long nitems = mf_item_count(Nt, true);
+  for (long long k = gw; k < nitems; k += nw) {
+    int j, i0;
+    mf_item(k, Nt, true, j, i0);
+    int irow[2];
+    mf_window_rows(op.prow, i0, lane, j, irow);
+    for (int c = 0; c < cols; ++c) {
+      const double2* xc = x + c * n;
+      double2* yc = y + c * n;
       double ox[2], oy[2];
-      mf_window_rows(op.prow, i0, lane, j, irow);
-      mf_window_apply<double, double2, ADJ>(op, x, j, i0, irow, ox, oy);
+      mf_window_apply<double, double2, ADJ>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int i = irow[u];
         if (i < 0) continue;
         if (i == j) {
-          y[i + (long long)Nt * j] = make_double2(ox[u], 0.0);
+          yc[i + (long long)Nt * j] = make_double2(ox[u], 0.0);
         } else {
-          y[i + (long long)Nt * j] = make_double2(ox[u], oy[u]);
-          y[j + (long long)Nt * i] = make_double2(ox[u], -oy[u]);
+          yc[i + (long long)Nt * j] = make_double2(ox[u], oy[u]);
+          yc[j + (long long)Nt * i] = make_double2(ox[u], -oy[u]);
         }
       }
     }
@@ -600,21 +609,34 @@ struct Estimator {
   // upper-triangle products).
   void mult(bool adjoint, int p, const double2* in, double2* out_, double2* tmp, int cols,
             int herm_cols = 0) {
-    if (herm_cols > 0 && (box_ok || op->gq.active)) {
-      const unsigned grid = (unsigned)std::min(Nt, 152 * 8);
+    if (herm_cols > 0 && box_ok) {
+      // every Hermitian column in one launch per power
+      const int hc = std::min(herm_cols, cols);
+      const long long items = mf_item_count(Nt, true);
+      const unsigned grid =
+          (unsigned)std::max<long long>(1, std::min<long long>((items + kBoxWarps - 1) / kBoxWarps,
+                                                               152 * 8));
+      const MfOp<double> m = make_mf<double>(*op, adjoint);
       const double2* src = in;
       for (int k = 0; k < p; ++k) {
         double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
-        if (op->gq.active) {
-          gq_apply_herm64(*op, adjoint, reinterpret_cast<const double*>(src),
-                          reinterpret_cast<double*>(dst));
-        } else {
-          const MfOp<double> m = make_mf<double>(*op, adjoint);
-          if (adjoint)
-            QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
-          else
-            QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, src, dst);
-        }
+        if (adjoint)
+          QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, hc, (long long)n, src, dst);
+        else
+          QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, hc, (long long)n, src, dst);
+        src = dst;
+      }
+      QSW_CUDA_TRY(cudaGetLastError());
+      if (cols > hc) mult(adjoint, p, in + (size_t)n * hc, out_ + (size_t)n * hc,
+                          tmp ? tmp + (size_t)n * hc : nullptr, cols - hc, 0);
+      return;
+    }
+    if (herm_cols > 0 && op->gq.active) {
+      const double2* src = in;
+      for (int k = 0; k < p; ++k) {
+        double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
+        gq_apply_herm64(*op, adjoint, reinterpret_cast<const double*>(src),
+                        reinterpret_cast<double*>(dst));
         src = dst;
       }
       QSW_CUDA_TRY(cudaGetLastError());
