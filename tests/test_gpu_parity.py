@@ -404,3 +404,23 @@ def test_empty_graph_is_static(ctx):
         # L~ = 0; the Hermitian form returns the Hermitian part of rho0 (numpy's
         # rho0 is Hermitian only to ~1e-17)
         assert np.max(np.abs(states.cpu().numpy() - W.vec(rho0)[None, :])) <= 1e-15
+
+
+def test_rejects_operator_beyond_32bit_indices(ctx):
+    # N~^2 must fit the 32-bit element indices: 46341^2 = 2,147,488,281 >= 2^31 - 1.
+    # The check runs on the host before any device work; the context stays usable.
+    from paper_2003_02450_gb300 import qsw as C
+    n = 46341
+    g = W.Digraph(n, np.zeros(n + 1, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    with pytest.raises(C.QswError) as e:
+        C.qsw_build_superoperator(ctx.handle, g, None, 0.5)
+    assert e.value.name == "QSW_ERR_TOO_LARGE"
+    # one source port pushes a graph just below the limit over it (N~ = N + ports)
+    g2 = W.Digraph(n - 1, np.zeros(n, np.int32), np.zeros(0, np.int32), np.zeros(0))
+    with pytest.raises(C.QswError) as e:
+        C.qsw_build_superoperator(ctx.handle, g2, None, 0.5, sources=[(0, 0.5)])
+    assert e.value.name == "QSW_ERR_TOO_LARGE"
+    w = _gpu(ctx, W.cycle_graph(6), 0.5)
+    w.initial_state(populations=[1, 0, 0, 0, 0, 0])
+    _, pops = w.series(0.0, 0.5, 3)
+    assert abs(float(pops[-1].sum().item()) - 1.0) <= 1e-12
