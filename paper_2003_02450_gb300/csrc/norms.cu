@@ -10,7 +10,16 @@
 //   SplitMix64 generator (Steele, Lea & Flood 2014) at a fixed seed; ties in
 //   the row-norm ranking go to the smaller index.
 //
-// Every product and reduction runs in FP64 on the device; the host only
+// The products that give the estimates (Y = A^p X and its column norms) run in
+// FP64 on the device, so every estimate is the FP64 1-norm of A^p x for a
+// column x the algorithm tried.  The adjoint step Z = (A^H)^p sign(Y) only
+// ranks the rows of Z by their largest modulus (which unit vectors to try
+// next, and the stop test on the best one); for the matrix-free L-QSW
+// operator it runs in complex64 with FP32 coefficients, scaled by 1/||A||_1
+// per product.  Where rounding at that precision reorders two nearly equal
+// row maxima, the estimator follows another branch Algorithm 2.4 allows; the
+// GB300's FP32 pipe issues 64 times the FP64 rate, which takes the adjoint
+// products off the FP64 pipe that bounds every other product.  The host only
 // follows the algorithm's branches on the few scalars each iteration returns
 // (one read-back for the column norms, one for the row ranking).
 // All reductions use a fixed grid and a fixed summation order, so repeated
@@ -180,6 +189,40 @@ __global__ void rowmax_kernel(int n, int t, const double2* __restrict__ Z, doubl
     double v = cabs_fast(Z[r]);
     if (t > 1) v = fmax(v, cabs_fast(Z[n + r]));
     h[r] = v;
+  }
+}
+
+// The adjoint step's ranking products run in complex64 (below, Estimator::
+// rank32): S = sign(Y) rounded to complex64.  Y is scaled by the power of two
+// that brings its larger component into [1, 2) (exact), so the rounding loses
+// neither range nor the direction; sign(0) = 1.  The map commutes with complex
+// conjugation (a Hermitian Y gives an exactly Hermitian S).
+__device__ __forceinline__ float2 sign32(double2 y) {
+  const double m = fmax(fabs(y.x), fabs(y.y));
+  if (m == 0.0) return make_float2(1.0f, 0.0f);
+  const int ex = (int)((__double_as_longlong(m) >> 52) & 0x7ff);
+  if (ex == 0 || ex > 2045) {   // subnormal, near overflow or not finite: the FP64 form
+    const double a = cabs_fast(y);
+    return make_float2((float)(y.x / a), (float)(y.y / a));
+  }
+  const double f = __longlong_as_double((long long)(2046 - ex) << 52);   // 2^(1023 - ex)
+  const float a = (float)(y.x * f), b = (float)(y.y * f);
+  const float r = rsqrtf(fmaf(a, a, b * b));
+  return make_float2(a * r, b * r);
+}
+
+__global__ void sign32_kernel(long long m, const double2* __restrict__ Y, float2* __restrict__ S) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x)
+    S[e] = sign32(Y[e]);
+}
+
+__global__ void rowmax32_kernel(int n, int t, const float2* __restrict__ Z, double* __restrict__ h) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < n;
+       r += (long long)gridDim.x * blockDim.x) {
+    float v = hypotf(Z[r].x, Z[r].y);
+    if (t > 1) v = fmaxf(v, hypotf(Z[n + r].x, Z[n + r].y));
+    h[r] = (double)v;
   }
 }
 
@@ -457,17 +500,23 @@ mf_box_kernel(MfOp<double> op, const int* __restrict__ list, const int* __restri
   }
 }
 
+__device__ __forceinline__ double2 cmake(double x, double y) { return make_double2(x, y); }
+__device__ __forceinline__ float2 cmake(float x, float y) { return make_float2(x, y); }
+
 // y_c = L~ x_c (or L~^H x_c) for `cols` Hermitian vectors stored n apart; both
 // maps preserve Hermiticity, so only the upper triangle is computed (the same
 // per-element helpers and order as the full product) and mirrored.  The
 // diagonal's imaginary part, zero in exact arithmetic, is stored as zero,
 // which keeps y exactly Hermitian.  Warps stride over the upper triangle's
 // 64-row windows (nearly equal work each); every window is applied to all
-// columns while its rows and neighbour lists are at hand.
-template <bool ADJ>
+// columns while its rows and neighbour lists are at hand.  The complex64 form
+// (the ranking products of the adjoint step) multiplies by `scale`; the
+// complex128 form ignores it.
+template <class R, class VT, bool ADJ>
 __global__ void __launch_bounds__(kBoxBlock)
-mf_herm_kernel(MfOp<double> op, int cols, long long n, const double2* __restrict__ x,
-               double2* __restrict__ y) {
+mf_herm_kernel(MfOp<R> op, int cols, long long n, R scale, const VT* __restrict__ x,
+               VT* __restrict__ y) {
+  constexpr bool kScaled = sizeof(R) == sizeof(float);
   const int Nt = op.Nt;
   const int lane = threadIdx.x & 31;
   const long long gw = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
@@ -479,19 +528,23 @@ mf_herm_kernel(MfOp<double> op, int cols, long long n, const double2* __restrict
     int irow[2];
     mf_window_rows(op.prow, i0, lane, j, irow);
     for (int c = 0; c < cols; ++c) {
-      const double2* xc = x + c * n;
-      double2* yc = y + c * n;
-      double ox[2], oy[2];
-      mf_window_apply<double, double2, ADJ>(op, xc, j, i0, irow, ox, oy);
+      const VT* xc = x + c * n;
+      VT* yc = y + c * n;
+      R ox[2], oy[2];
+      mf_window_apply<R, VT, ADJ>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int i = irow[u];
         if (i < 0) continue;
+        if (kScaled) {
+          ox[u] *= scale;
+          oy[u] *= scale;
+        }
         if (i == j) {
-          yc[i + (long long)Nt * j] = make_double2(ox[u], 0.0);
+          yc[i + (long long)Nt * j] = cmake(ox[u], R(0));
         } else {
-          yc[i + (long long)Nt * j] = make_double2(ox[u], oy[u]);
-          yc[j + (long long)Nt * i] = make_double2(ox[u], -oy[u]);
+          yc[i + (long long)Nt * j] = cmake(ox[u], oy[u]);
+          yc[j + (long long)Nt * i] = cmake(ox[u], -oy[u]);
         }
       }
     }
@@ -519,9 +572,9 @@ __global__ void sign_minus_one_kernel(int Nt, const int* __restrict__ list,
 }
 
 // out = in^dag for N~ x N~ matrices (column-major), through 32 x 32 tiles.
-__global__ void conj_transpose_kernel(int Nt, const double2* __restrict__ in,
-                                      double2* __restrict__ out) {
-  __shared__ double2 tile[32][33];
+template <class VT>
+__global__ void conj_transpose_kernel(int Nt, const VT* __restrict__ in, VT* __restrict__ out) {
+  __shared__ VT tile[32][33];
   const int tiles = (Nt + 31) / 32;
   for (long long b = blockIdx.x; b < (long long)tiles * tiles; b += gridDim.x) {
     const int bi = (int)(b % tiles) * 32, bj = (int)(b / tiles) * 32;
@@ -533,8 +586,8 @@ __global__ void conj_transpose_kernel(int Nt, const double2* __restrict__ in,
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
       const int i = bj + threadIdx.x, j = bi + r;   // out(i, j) = conj(in(j, i))
       if (i < Nt && j < Nt) {
-        const double2 v = tile[threadIdx.x][r];
-        out[i + (long long)Nt * j] = make_double2(v.x, -v.y);
+        const VT v = tile[threadIdx.x][r];
+        out[i + (long long)Nt * j] = cmake(v.x, -v.y);
       }
     }
     __syncthreads();
@@ -593,7 +646,10 @@ struct Estimator {
   const Csr* A;    // CSR operator, or null for matrix-free
   const Csr* AH;
   DevBuf X, Y, W, h, partials, pv, pi, out, sel;
+  DevBuf S32, Z32, T32;     // complex64 ranking products of the adjoint step
+  double inv_one = 1.0;     // 1 / ||L||_1: their per-product scale
   bool box_ok = false;      // matrix-free L-QSW: unit chains track their box
+  bool rank32 = false;      // ... and the adjoint step ranks rows in complex64
   bool split_ok = false;    // ... and the adjoint step may split off (A^H)^p 1
   Chain chains[kChainsMax];
   int n_chains = 2;
@@ -621,9 +677,11 @@ struct Estimator {
       for (int k = 0; k < p; ++k) {
         double2* dst = ((p - k) % 2 == 1) ? out_ : tmp;
         if (adjoint)
-          QSW_LAUNCH mf_herm_kernel<true><<<grid, kBoxBlock, 0, st>>>(m, hc, (long long)n, src, dst);
+          QSW_LAUNCH mf_herm_kernel<double, double2, true><<<grid, kBoxBlock, 0, st>>>(
+              m, hc, (long long)n, 1.0, src, dst);
         else
-          QSW_LAUNCH mf_herm_kernel<false><<<grid, kBoxBlock, 0, st>>>(m, hc, (long long)n, src, dst);
+          QSW_LAUNCH mf_herm_kernel<double, double2, false><<<grid, kBoxBlock, 0, st>>>(
+              m, hc, (long long)n, 1.0, src, dst);
         src = dst;
       }
       QSW_CUDA_TRY(cudaGetLastError());
@@ -762,11 +820,41 @@ struct Estimator {
   }
 
   // column 1 of a block = column 0 ^dag
-  void mirror_column() {
+  void mirror_column(bool z32 = false) {
     const int tiles = (Nt + 31) / 32;
-    QSW_LAUNCH conj_transpose_kernel<<<(unsigned)std::min<long long>((long long)tiles * tiles, 4096),
-                                       dim3(32, 8), 0, st>>>(Nt, Y.as<double2>(),
-                                                             Y.as<double2>() + (size_t)n);
+    const unsigned grid = (unsigned)std::min<long long>((long long)tiles * tiles, 4096);
+    if (z32)
+      QSW_LAUNCH conj_transpose_kernel<float2><<<grid, dim3(32, 8), 0, st>>>(
+          Nt, Z32.as<float2>(), Z32.as<float2>() + (size_t)n);
+    else
+      QSW_LAUNCH conj_transpose_kernel<double2><<<grid, dim3(32, 8), 0, st>>>(
+          Nt, Y.as<double2>(), Y.as<double2>() + (size_t)n);
+    QSW_CUDA_TRY(cudaGetLastError());
+  }
+
+  // Z32 = ((A^H / ||A||_1)^p S32) for `cols` columns of S32 (the first
+  // herm_cols Hermitian: upper-triangle products), in complex64.  Only the
+  // ranking of the rows of Z by their largest modulus is used, which the
+  // positive scale leaves as it is; with it |Z| <= 1 (||A^H||_inf = ||A||_1,
+  // |sign| = 1), so no power overflows the FP32 range.
+  void mult32_adjoint(int p, int cols, int herm_cols) {
+    const float scale = (float)inv_one;
+    const float2* src = S32.as<float2>();
+    for (int k = 0; k < p; ++k) {
+      float2* dst = ((p - k) % 2 == 1) ? Z32.as<float2>() : T32.as<float2>();
+      if (herm_cols > 0) {
+        const long long items = mf_item_count(Nt, true);
+        const unsigned grid = (unsigned)std::max<long long>(
+            1, std::min<long long>((items + kBoxWarps - 1) / kBoxWarps, 152 * 8));
+        const MfOp<float> m = make_mf<float>(*op, true);
+        QSW_LAUNCH mf_herm_kernel<float, float2, true><<<grid, kBoxBlock, 0, st>>>(
+            m, cols, (long long)n, scale, src, dst);
+      } else {
+        mf_apply32(*op, true, cols, reinterpret_cast<const float*>(src),
+                   reinterpret_cast<float*>(dst), scale);
+      }
+      src = dst;
+    }
     QSW_CUDA_TRY(cudaGetLastError());
   }
 
@@ -914,15 +1002,25 @@ struct Estimator {
       bool split = k >= 2 && split_ok;
       for (int c = 0; c < tz && split; ++c)
         split = ych[c]->box && !ych[c]->full && ych[c]->box_elems * 16 <= (long long)n;
+      bool z32 = false;
       if (split) {
         adjoint_split(p, ych, tz);
+      } else if (rank32) {
+        QSW_LAUNCH sign32_kernel<<<grid_for((long long)n * tz, 256, 4096), 256, 0, st>>>(
+            (long long)n * tz, Yp, S32.as<float2>());
+        mult32_adjoint(p, tz, k == 1 ? tz : 0);   // k = 1: sign(Y) is Hermitian
+        z32 = true;
       } else {
         QSW_LAUNCH sign_kernel<<<grid_for((long long)n * tz, 256, 4096), 256, 0, st>>>(
             (long long)n * tz, Yp, Xp);
         mult(true, p, Xp, Yp, Wp, tz, k == 1 ? tz : 0);   // k = 1: sign(Y) is Hermitian
       }
-      if (mirror) mirror_column();
-      QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
+      if (mirror) mirror_column(z32);
+      if (z32)
+        QSW_LAUNCH rowmax32_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Z32.as<float2>(),
+                                                                           h.as<double>());
+      else
+        QSW_LAUNCH rowmax_kernel<<<grid_for(n, 256, 4096), 256, 0, st>>>(n, t, Yp, h.as<double>());
       QSW_CUDA_TRY(cudaGetLastError());
       Select pick;
       select(hist, ind_best, &pick);
@@ -994,6 +1092,12 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.sel.alloc(sizeof(Select));
   E.Nt = op.Nt;
   E.box_ok = !L && !op.gq.active;
+  E.rank32 = E.box_ok;
+  if (E.rank32) {
+    E.S32.alloc(sizeof(float2) * (size_t)n * E.t);
+    E.Z32.alloc(sizeof(float2) * (size_t)n * E.t);
+    E.T32.alloc(sizeof(float2) * (size_t)n * E.t);
+  }
   E.split_ok = E.box_ok &&
                sizeof(double2) * (size_t)n * (kNormPowers + 1) <= kOnesChainBytes;
   E.n_chains = (int)std::min<size_t>(
@@ -1005,6 +1109,7 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
     E.start_chain();
   }
   op.norms[0] = one;
+  E.inv_one = one > 0.0 ? 1.0 / one : 1.0;
   for (int p = 2; p <= kNormPowers; ++p) op.norms[p - 1] = one == 0.0 ? 0.0 : E.estimate(p);
 
   // d_p = ||L^p||_1^(1/p), taken on the device; the host keeps a copy for sizing.

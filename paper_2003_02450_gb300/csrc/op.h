@@ -163,6 +163,7 @@ double op_bytes(const Op& op);
 template <class R> struct MfOp;
 template <class R> MfOp<R> make_mf(const Op& op, bool adjoint);
 void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale);
+void mf_apply32(const Op& op, bool adjoint, int cols, const float* x, float* y, double scale);
 int choose_tpr(double avg_row);
 void tune_csr_schedule(Op& op);  // autotuned lanes per row and unroll (cached per bucket)
 long long tune_measurements();   // schedule measurements made in this process

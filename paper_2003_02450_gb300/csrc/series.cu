@@ -979,6 +979,20 @@ void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
+// The same in complex64 with the FP32 coefficients (the 1-norm estimator's
+// ranking products).
+void mf_apply32(const Op& op, bool adjoint, int cols, const float* x, float* y, double scale) {
+  const MfOp<float> m = make_mf<float>(op, adjoint);
+  const unsigned grid = (unsigned)std::min(op.Nt, 152 * 8);
+  if (adjoint)
+    QSW_LAUNCH mf_apply_kernel<float, float2, true><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), scale);
+  else
+    QSW_LAUNCH mf_apply_kernel<float, float2, false><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), scale);
+  QSW_CUDA_TRY(cudaGetLastError());
+}
+
 double op_bytes(const Op& op) {
   const bool f32 = op.precision == QSW_C64_BULK;
   if (op.gq.active)   // Q and L' rows: column index + complex value
