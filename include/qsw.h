@@ -86,6 +86,16 @@ typedef enum { QSW_OPERATOR_MATRIX_FREE = 0, QSW_OPERATOR_CSR = 1 } qsw_operator
  * row instead of the tuned value; see qsw_op_schedule). */
 #define QSW_BUILD_FIXED_SCHEDULE 0x200
 
+/* OR-ed into operator_kind: take every product of the 1-norm estimator in
+ * complex128.  By default the matrix-free L-QSW operator runs the adjoint
+ * step Z = (L~^H)^p sign(Y) of Higham & Tisseur's Algorithm 2.4 in complex64:
+ * Z only ranks rows (which unit vectors to try next, and the stop test on the
+ * best one), while every estimate is the complex128 1-norm of L~^p x for a
+ * column x the algorithm tried.  Both forms return estimates the algorithm
+ * can return; they may follow different branches where two row maxima are
+ * within complex64 rounding of each other. */
+#define QSW_BUILD_FP64_RANKING 0x400
+
 typedef struct qsw_ctx qsw_ctx;   /* device + stream + workspace cache */
 typedef struct qsw_op qsw_op;     /* one assembled superoperator L~ */
 

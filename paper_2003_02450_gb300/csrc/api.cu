@@ -276,7 +276,8 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
                   "unknown precision");
     const bool defer = (operator_kind & QSW_BUILD_DEFER_NORMS) != 0;
     const bool fixed_schedule = (operator_kind & QSW_BUILD_FIXED_SCHEDULE) != 0;
-    operator_kind &= ~(QSW_BUILD_DEFER_NORMS | QSW_BUILD_FIXED_SCHEDULE);
+    const bool rank64 = (operator_kind & QSW_BUILD_FP64_RANKING) != 0;
+    operator_kind &= ~(QSW_BUILD_DEFER_NORMS | QSW_BUILD_FIXED_SCHEDULE | QSW_BUILD_FP64_RANKING);
     QSW_CHECK_ARG(operator_kind == QSW_OPERATOR_MATRIX_FREE || operator_kind == QSW_OPERATOR_CSR,
                   QSW_ERR_INVALID_ARG, "unknown operator kind");
     QSW_CHECK_ARG(!defer || operator_kind == QSW_OPERATOR_MATRIX_FREE, QSW_ERR_INVALID_ARG,
@@ -306,6 +307,7 @@ qsw_status qsw_build_superoperator(qsw_ctx* ctx, const qsw_csr* G, const qsw_csr
       op->tpr_fixed = true;
       op->tpr = 0;
     }
+    op->rank64 = rank64;
     op->omega = omega;
     op->N = G->n;
     op->Nt = (int)Nt;

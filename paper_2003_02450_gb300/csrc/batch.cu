@@ -619,6 +619,10 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
       for (int u = 0; u < kBKReg; ++u) fmx[u] = 0;
       // the new term at element (i, j) (all n0 columns): store it (and its
       // mirror), fold it into the running maxima and the active outputs
+      // The output updates are read-modify-writes of the ring (L2); the
+      // compiler cannot move a read above a store to the same array, so the
+      // n0 reads of one accumulator are issued together before its stores
+      // (one round trip per output instead of one per right-hand side).
       auto element = [&](int i, int j, const Rt* yx, const Rt* yy) {
         const long long r = i + (long long)Nt * j;
         NT rs = 0;
@@ -633,36 +637,27 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
           dy[c] = (double)ay;
         }
         kmax = NA::vmax(kmax, rs);
-#pragma unroll
-        for (int u2 = 0; u2 < kBKReg; ++u2) {
-          if (!own[u2]) continue;
-          double2* F = fslot(J.out_index0 + u2);
-          NT fs = 0;
-#pragma unroll
-          for (int c = 0; c < N0; ++c) {
-            double2 f = ldf<SK>(F + c * n + r);
-            f.x = fma(coef[u2], dx[c], f.x);
-            f.y = fma(coef[u2], dy[c], f.y);
-            F[c * n + r] = f;
-            fs += NA::of(f.x, f.y);
-          }
-          fmx[u2] = NA::vmax(fmx[u2], fs);
-        }
-        for (int k = kBKReg; k < J.d; ++k) {
-          if (!s_active[k]) continue;
-          const double ck = s_coef[k];
+        auto update = [&](int k, double ck) -> NT {
           double2* F = fslot(J.out_index0 + k);
+          double2 f[N0];
+#pragma unroll
+          for (int c = 0; c < N0; ++c) f[c] = ldf<SK>(F + c * n + r);
           NT fs = 0;
 #pragma unroll
           for (int c = 0; c < N0; ++c) {
-            double2 f = ldf<SK>(F + c * n + r);
-            f.x = fma(ck, dx[c], f.x);
-            f.y = fma(ck, dy[c], f.y);
-            F[c * n + r] = f;
-            fs += NA::of(f.x, f.y);
+            f[c].x = fma(ck, dx[c], f[c].x);
+            f[c].y = fma(ck, dy[c], f[c].y);
+            fs += NA::of(f[c].x, f[c].y);
           }
-          atomicMax(&s_extra[k], bits_of((double)fs));
-        }
+#pragma unroll
+          for (int c = 0; c < N0; ++c) F[c * n + r] = f[c];
+          return fs;
+        };
+#pragma unroll
+        for (int u2 = 0; u2 < kBKReg; ++u2)
+          if (own[u2]) fmx[u2] = NA::vmax(fmx[u2], update(u2, coef[u2]));
+        for (int k = kBKReg; k < J.d; ++k)
+          if (s_active[k]) atomicMax(&s_extra[k], bits_of((double)update(k, s_coef[k])));
       };
       if (SK) {
         // one CTA, terms on chip: one thread per element (upper triangle in

@@ -1092,7 +1092,7 @@ void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   E.sel.alloc(sizeof(Select));
   E.Nt = op.Nt;
   E.box_ok = !L && !op.gq.active;
-  E.rank32 = E.box_ok;
+  E.rank32 = E.box_ok && !op.rank64;
   if (E.rank32) {
     E.S32.alloc(sizeof(float2) * (size_t)n * E.t);
     E.Z32.alloc(sizeof(float2) * (size_t)n * E.t);

@@ -114,6 +114,7 @@ struct Op {
   int csr_unroll = 2;       // CSR sweep: entries per lane in flight (2 or 4)
   bool tpr_fixed = false;   // set: keep tpr and csr_unroll (tuned, or QSW_BUILD_FIXED_SCHEDULE)
   bool norms_ready = false;
+  bool rank64 = false;      // QSW_BUILD_FP64_RANKING: the estimator's adjoint step in FP64
 
   // series workspace
   DevBuf kbuf, ring, jobs, ctrl, scratch;

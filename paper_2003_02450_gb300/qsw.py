@@ -77,6 +77,7 @@ class qsw_batch_stats(ctypes.Structure):
 
 QSW_BUILD_DEFER_NORMS = 0x100
 QSW_BUILD_FIXED_SCHEDULE = 0x200
+QSW_BUILD_FP64_RANKING = 0x400
 NOALLOC_SCRATCH_BYTES = 16 << 20   # QSW_NOALLOC_SCRATCH_BYTES
 
 
@@ -259,14 +260,15 @@ def qsw_last_error(ctx) -> str:
 
 def qsw_build_superoperator(ctx, G, H=None, omega: float = 0.5, sources=(), sinks=(),
                             precision="c128", operator="matfree", defer_norms: bool = False,
-                            fixed_schedule: bool = False):
+                            fixed_schedule: bool = False, fp64_ranking: bool = False):
     g = _as_csr(G)
     h = _as_csr(H)
     src, nsrc = _ports(sources)
     snk, nsnk = _ports(sinks)
     prec = PRECISIONS.get(precision, precision)
     kind = (OPERATORS.get(operator, operator) | (QSW_BUILD_DEFER_NORMS if defer_norms else 0)
-            | (QSW_BUILD_FIXED_SCHEDULE if fixed_schedule else 0))
+            | (QSW_BUILD_FIXED_SCHEDULE if fixed_schedule else 0)
+            | (QSW_BUILD_FP64_RANKING if fp64_ranking else 0))
     op = c_void_p()
     st = lib().qsw_build_superoperator(ctx, byref(g.c), byref(h.c) if h else None, float(omega),
                                        src, nsrc, snk, nsnk, int(prec), int(kind), byref(op))

@@ -149,3 +149,31 @@ def test_global_walk_norm_series_is_an_estimator_outcome(ctx, kind, omega, sourc
     again = np.asarray(C.qsw_op_info(ctx.handle, op)["norms"])
     C.qsw_op_destroy(op)
     assert np.array_equal(again, got)
+
+
+@pytest.mark.parametrize("kind,omega,sources,sinks", CASES[:1] + CASES[3:])
+def test_fp64_ranking_flag_gives_estimator_outcomes(ctx, kind, omega, sources, sinks):
+    """QSW_BUILD_FP64_RANKING keeps the adjoint step of every estimate in
+    complex128; the default ranks rows in complex64.  Both return values the
+    estimator can return (FP64 norms of tried columns), both repeatably."""
+    from paper_2003_02450_gb300 import qsw as C
+    g = _graph(kind)
+    vals = _exact(kind, omega, tuple(sources), tuple(sinks))
+    got = {}
+    for rank64 in (False, True):
+        runs = []
+        for _ in range(2):
+            op = C.qsw_build_superoperator(ctx.handle, g, None, omega, sources, sinks,
+                                           fp64_ranking=rank64)
+            runs.append(np.asarray(C.qsw_op_info(ctx.handle, op)["norms"]))
+            C.qsw_op_destroy(op)
+        assert np.array_equal(runs[0], runs[1])
+        got[rank64] = runs[0]
+        for p in range(2, 10):
+            exact, v = vals[p]
+            est = runs[0][p - 1]
+            assert exact / 10 <= est <= exact * (1 + 1e-12)
+            k = np.searchsorted(v, est)
+            near = min(abs(v[max(k - 1, 0)] - est), abs(v[min(k, v.size - 1)] - est))
+            assert near <= 1e-10 * exact, (rank64, p, est, exact)
+    assert got[False][0] == got[True][0]
