@@ -921,7 +921,12 @@ def run_batch_workload(args):
             "config": {"workload": "batch256", "walks": len(walks), "rhs_per_walk": n0,
                        "steps": q, "dt": dt, "clusters": s0["clusters"]},
             "batch": {"norms_ms": s0["norms_ms"], "series_ms": s0["series_ms"],
-                      "matvecs": s0["matvecs"], "fupdates": s0["fupdates"]},
+                      "matvecs": s0["matvecs"], "fupdates": s0["fupdates"],
+                      "schedule": {"cluster_size": s0["cluster_size"],
+                                   "small_limit_bytes": s0["small_limit"],
+                                   "how": "autotuned on the first (warm-up) step: every "
+                                          "candidate (clusters of 4/8/16 CTAs x one-CTA "
+                                          "limit 0/32/64 KB) timed on this batch"}},
             "roofline": {
                 "bound": "latency (FP32 operator products + FP64 output sums, L2-resident terms)",
                 "kernel": "batch_series_kernel + batch_small_kernel (series phase)",

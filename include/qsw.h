@@ -329,6 +329,10 @@ typedef struct {
   double algorithmic_bytes;  /* series phase, all walks: operator data, term
                                 read and written, output updates per
                                 application, as in qsw_series_stats */
+  int32_t cluster_size;      /* the series phase's schedule: CTAs per cluster */
+  int32_t small_limit;       /* ... and the largest pair of Taylor-term blocks
+                                (bytes) run by one CTA (0: none) */
+  int32_t tuned;             /* 1: this call timed the candidate schedules */
 } qsw_batch_stats;
 
 /* Many independent walks in one launch (not in the paper): walk w is `ops[w]`
@@ -348,6 +352,23 @@ qsw_status qsw_batch_series(qsw_ctx* ctx, int32_t count, qsw_op* const* ops,
                             const double* const* d_rho0, int32_t n0, const double* t0,
                             const double* dt, const int32_t* steps, double* const* d_pops,
                             qsw_batch_stats* stats);
+
+/* The series phase's schedule for this context's batched calls.  By default
+ * (cluster_size 0, small_limit -1) it is autotuned: the first batch of a kind
+ * (n0, the precisions present, the largest N~ and the walk count, each by
+ * power of two) with at least 16 walks times its own series phase under every
+ * candidate (clusters of 4, 8 or 16 CTAs x one-CTA limit 0, 32 or 64 KB),
+ * keeps the fastest for the process and counts one measurement
+ * (qsw_tune_measurements); smaller batches run clusters of 8 and a 64 KB
+ * limit.  A walk's populations do not depend on the schedule (same
+ * per-element arithmetic; the phase's cluster reductions are maxima).
+ * cluster_size: 0 (tuned) or 2, 4, 8, 16; small_limit: -1 (tuned) or 0 ..
+ * 65536 bytes (walks whose two Taylor-term blocks, 2 n0 n_w values of the
+ * walk's precision, fit run on one thread block with the terms in shared
+ * memory).  A fixed value replaces only its own half of the pair: the other
+ * half is the tuned one when this kind of batch has been tuned, else the
+ * default; no call tunes while either half is fixed.  Errors: INVALID_ARG. */
+qsw_status qsw_batch_set_schedule(qsw_ctx* ctx, int32_t cluster_size, int32_t small_limit);
 
 /* ------------------------------------------ global-interaction walks */
 
@@ -454,8 +475,11 @@ qsw_status qsw_probe_wait_limit(qsw_ctx* ctx, double* seconds);
  * request's host buffer.  Requests arriving while batches run are launched by
  * another worker on its own stream, so their work overlaps on the device.  A
  * request's populations do not depend on which other requests share its
- * batch.  memory_budget_bytes = 0 selects half of the free device memory; a
- * request larger than the budget runs alone. */
+ * batch.  A worker's batches take the series-phase schedule tuned for their
+ * kind by earlier qsw_batch_series calls in the process (the default when
+ * there is none): a worker never stalls a batch to time candidates.
+ * memory_budget_bytes = 0 selects half of the free device memory; a request
+ * larger than the budget runs alone. */
 typedef struct {
   int32_t workers;             /* concurrent batches (streams), >= 1; 0 -> 2 */
   int32_t max_batch;           /* requests per batched launch; 0 -> 64 */
@@ -524,11 +548,13 @@ int64_t qsw_device_allocations(void);
  * parity bound).  The no-allocation entry point never tunes: it uses the
  * operator's current value. */
 
-/* Number of schedule measurements (one per tuned bucket) made in this
- * process.  Pure host call. */
+/* Number of schedule measurements (one per tuned CSR bucket, and one per
+ * tuned kind of batch: qsw_batch_set_schedule) made in this process.  Pure
+ * host call. */
 int64_t qsw_tune_measurements(void);
-/* Forget every tuned schedule (the next CSR operator of each bucket is
- * measured again).  Pure host call; not safe against concurrent series. */
+/* Forget every tuned schedule (the next CSR operator of each bucket, and the
+ * next batch of each kind, is measured again).  Pure host call; not safe
+ * against concurrent series. */
 void qsw_tune_reset(void);
 /* The operator's CSR schedule (0 and 0 for a matrix-free operator): lanes
  * per row and the row loop's unroll depth (2 or 4 entries per lane in flight;

@@ -704,9 +704,27 @@ int64_t qsw_kernel_launches(void) { return qsw::g_launches.load(); }
 
 int64_t qsw_device_allocations(void) { return qsw::g_device_allocs.load(); }
 
-int64_t qsw_tune_measurements(void) { return qsw::tune_measurements(); }
+int64_t qsw_tune_measurements(void) {
+  return qsw::tune_measurements() + qsw::batch_tune_measurements();
+}
 
-void qsw_tune_reset(void) { qsw::tune_reset(); }
+void qsw_tune_reset(void) {
+  qsw::tune_reset();
+  qsw::batch_tune_reset();
+}
+
+qsw_status qsw_batch_set_schedule(qsw_ctx* ctx, int32_t cluster_size, int32_t small_limit) {
+  return guarded(ctx, [&] {
+    QSW_CHECK_ARG(ctx != nullptr, QSW_ERR_INVALID_ARG, "ctx is NULL");
+    QSW_CHECK_ARG(cluster_size == 0 || cluster_size == 2 || cluster_size == 4 ||
+                      cluster_size == 8 || cluster_size == 16,
+                  QSW_ERR_INVALID_ARG, "cluster_size must be 0, 2, 4, 8 or 16");
+    QSW_CHECK_ARG(small_limit >= -1 && small_limit <= 65536, QSW_ERR_INVALID_ARG,
+                  "small_limit must be -1 or 0 .. 65536");
+    ctx->batch_cs = cluster_size;
+    ctx->batch_small = small_limit;
+  });
+}
 
 qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row, int32_t* csr_unroll) {
   if (!op || !csr_lanes_per_row) return QSW_ERR_INVALID_ARG;

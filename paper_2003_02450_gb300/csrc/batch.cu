@@ -28,6 +28,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <map>
 #include <mutex>
 #include <numeric>
 #include <thread>
@@ -135,13 +137,14 @@ struct Red {
 // barrier, partial results read through distributed shared memory) or one CTA.
 struct ClusterG {
   cg::cluster_group cl;
-  static constexpr int kSize = kCl;
+  int sz;   // CTAs in the cluster (phase 1: kCl; phase 2: the launch's cluster size)
+  __device__ int size() const { return sz; }
   __device__ int rank() const { return (int)cl.block_rank(); }
   __device__ void sync() { cl.sync(); }
   __device__ const Red* peer(Red& R, int r) { return cl.map_shared_rank(&R, r); }
 };
 struct CtaG {
-  static constexpr int kSize = 1;
+  __device__ int size() const { return 1; }
   __device__ int rank() const { return 0; }
   __device__ void sync() { __syncthreads(); }
   __device__ const Red* peer(Red& R, int) { return &R; }
@@ -209,7 +212,7 @@ __device__ void grp_max2(G& g, Red& R, double a, double b, double& oa, double& o
   g.sync();
   if (threadIdx.x == 0) {
     double s0 = 0, s1 = 0;
-    for (int r = 0; r < G::kSize; ++r) {
+    for (int r = 0; r < g.size(); ++r) {
       const Red* p = g.peer(R, r);
       s0 = dmax_bits(s0, p->blk[0]);
       s1 = dmax_bits(s1, p->blk[1]);
@@ -224,7 +227,7 @@ __device__ void grp_max2(G& g, Red& R, double a, double b, double& oa, double& o
 
 __device__ __forceinline__ void cl_max2(cg::cluster_group& cl, Red& R, double a, double b,
                                         double& oa, double& ob) {
-  ClusterG g{cl};
+  ClusterG g{cl, kCl};
   grp_max2(g, R, a, b, oa, ob);
 }
 
@@ -534,6 +537,84 @@ template <bool SK> __device__ __forceinline__ double2 ldf(const double2* p) {
   return __ldcg(p);
 }
 
+// All n0 right-hand sides of a walk in one pass over the operator's lists
+// (an SpMM): part B of C for the two rows of a lane, then part A, the
+// diagonal and the jumps for one row, every column at once, so the gathers
+// of the n0 columns are in flight together.  Per (row, column) the terms are
+// added in the same order as mf_partB / mf_finish / mf_tail.
+template <class R, class VT, int N0, class LD>
+__device__ __forceinline__ void bmf_partB(const MfOp<R>& op, const VT* __restrict__ x, long long n,
+                                          int j, const int* irow, R (*cx)[N0], R (*cy)[N0]) {
+#pragma unroll
+  for (int u = 0; u < 2; ++u)
+#pragma unroll
+    for (int c = 0; c < N0; ++c) { cx[u][c] = 0; cy[u][c] = 0; }
+  if (j >= op.N) return;
+  const int e0 = op.hrow[j], e1 = op.hrow[j + 1];
+  for (int e = e0; e < e1; ++e) {
+    const long long off = (long long)op.Nt * op.hcol[e];
+    const R h = op.hval[e];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (irow[u] < 0) continue;
+      VT v[N0];
+#pragma unroll
+      for (int c = 0; c < N0; ++c) v[c] = LD::ld(x + c * n + off + irow[u]);
+#pragma unroll
+      for (int c = 0; c < N0; ++c) {
+        cx[u][c] = fma(-h, v[c].x, cx[u][c]);
+        cy[u][c] = fma(-h, v[c].y, cy[u][c]);
+      }
+    }
+  }
+}
+
+template <class R, class VT, int N0, class LD>
+__device__ __forceinline__ void bmf_finish(const MfOp<R>& op, const VT* __restrict__ x, long long n,
+                                           int i, int j, R* cx, R* cy) {
+  const long long base = (long long)op.Nt * j;
+  if (i < op.N) {
+    const int e0 = op.hrow[i], e1 = op.hrow[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const long long a = base + op.hcol[e];
+      const R h = op.hval[e];
+      VT v[N0];
+#pragma unroll
+      for (int c = 0; c < N0; ++c) v[c] = LD::ld(x + c * n + a);
+#pragma unroll
+      for (int c = 0; c < N0; ++c) {
+        cx[c] = fma(h, v[c].x, cx[c]);
+        cy[c] = fma(h, v[c].y, cy[c]);
+      }
+    }
+  }
+  VT xs[N0];
+#pragma unroll
+  for (int c = 0; c < N0; ++c) xs[c] = LD::ld(x + c * n + base + i);
+  const R dx = op.ad[i] + op.ad[j];
+  const R dy = op.hw[j] - op.hw[i];
+#pragma unroll
+  for (int c = 0; c < N0; ++c) {   // -i C + D x
+    const R rx = fma(dx, xs[c].x, fma(-dy, xs[c].y, cy[c]));
+    const R ry = fma(dx, xs[c].y, fma(dy, xs[c].x, -cx[c]));
+    cx[c] = rx;
+    cy[c] = ry;
+  }
+  if (i == j) {
+    const int e0 = op.jrow[i], e1 = op.jrow[i + 1];
+    for (int e = e0; e < e1; ++e) {
+      const long long a = (long long)op.jcol[e] * (op.Nt + 1);
+      const R r = op.jval[e];
+#pragma unroll
+      for (int c = 0; c < N0; ++c) {
+        const VT v = LD::ld(x + c * n + a);
+        cx[c] = fma(r, v.x, cx[c]);
+        cy[c] = fma(r, v.y, cy[c]);
+      }
+    }
+  }
+}
+
 // Phase 2 of one walk on group g.  SK: the Taylor-term blocks live in shared
 // memory at `sk` (one-CTA groups); otherwise in the walk's workspace.
 template <class G, class VT, int N0, bool SK>
@@ -546,7 +627,7 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
   using LDP = typename std::conditional<SK, LdGeneric, LdGlobal>::type;
   const int crank = g.rank();
   const long long ct = (long long)crank * kBT + threadIdx.x;
-  const long long cstride = (long long)G::kSize * kBT;
+  const long long cstride = (long long)g.size() * kBT;
   const int Nt = W.Nt;
   const long long n = W.n;
   const bool herm = W.herm != 0;
@@ -685,7 +766,7 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
         }
       } else {
         const long long nitems = mf_item_count(Nt, herm);
-        for (long long it = gw; it < nitems; it += G::kSize * kBW) {
+        for (long long it = gw; it < nitems; it += (long long)g.size() * kBW) {
           int j, i0;
           mf_item(it, Nt, herm, j, i0);
           int irow[2];
@@ -695,19 +776,10 @@ __device__ __noinline__ void run_walk(G g, Red& R, const BWalk& W, double tol, d
             irow[u] = (i < Nt && (!herm || i <= j)) ? i : -1;
           }
           Rt yx[2][N0], yy[2][N0];
+          bmf_partB<Rt, VT, N0, LDP>(op, kc, n, j, irow, yx, yy);
 #pragma unroll
-          for (int c = 0; c < N0; ++c) {
-            Rt cx[2], cy[2];
-            mf_partB<Rt, VT, 2, LDP>(op, kc + c * n, j, irow, cx, cy);
-#pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              yx[u][c] = 0;
-              yy[u][c] = 0;
-              if (irow[u] >= 0)
-                mf_finish<Rt, VT, false, LDP>(op, kc + c * n, irow[u], j, cx[u], cy[u], yx[u][c],
-                                              yy[u][c]);
-            }
-          }
+          for (int u = 0; u < 2; ++u)
+            if (irow[u] >= 0) bmf_finish<Rt, VT, N0, LDP>(op, kc, n, irow[u], j, yx[u], yy[u]);
 #pragma unroll
           for (int u = 0; u < 2; ++u)
             if (irow[u] >= 0) element(irow[u], j, yx[u], yy[u]);
@@ -797,8 +869,11 @@ __device__ void dispatch_walk(G g, Red& R, const BWalk& W, double tol, double* s
 
 // 4 blocks per SM (64 registers): the walks' phase 2 is latency-bound on
 // gathers from L2, and twice the resident clusters outweigh the register
-// spills (batch256: 214 -> 180 ms for the series phase).
-__global__ void __cluster_dims__(kCl, 1, 1) __launch_bounds__(kBT, 4)
+// spills (batch256: 214 -> 180 ms for the series phase).  The cluster size is
+// the launch's (2, 4, 8 or 16 CTAs, chosen by the schedule tuner); a walk's
+// results do not depend on it (per-element arithmetic is the same, and the
+// cluster reductions of this phase are maxima).
+__global__ void __launch_bounds__(kBT, 4)
 batch_series_kernel(BArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ Red R;
@@ -822,8 +897,8 @@ batch_series_kernel(BArgs a) {
     cl.sync();
     if (__ldcg(&W.counters[2])) continue;   // L2 read: every CTA sees rank 0's flag
     const double tol = a.tol[W.f32 ? 1 : 0];
-    dispatch_walk<ClusterG, false>(ClusterG{cl}, R, W, tol, s_coef, s_step, s_c1, s_active,
-                                   nullptr);
+    dispatch_walk<ClusterG, false>(ClusterG{cl, (int)cl.num_blocks()}, R, W, tol, s_coef, s_step,
+                                   s_c1, s_active, nullptr);
   }
 }
 
@@ -899,7 +974,101 @@ void allow_small_smem(int device) {
   done[device] = true;
 }
 
+// ------------------------------------------------ series-phase schedule
+// The series phase's schedule: CTAs per cluster (cs) and the largest pair of
+// Taylor-term blocks (bytes) with which a walk runs on ONE CTA with its terms
+// in shared memory (small_limit; 0: every walk on a cluster).  A walk's
+// results do not depend on it (same per-element arithmetic; the phase's
+// cluster reductions are maxima), so the schedule is free to tune.  The first
+// batch of a kind (n0, precisions, largest N~ and walk count, each by power
+// of two) with at least kTuneMinWalks walks times its own series phase under
+// every candidate and keeps the fastest for the process; smaller batches take
+// kDefaultSched.
+struct BSched {
+  int cs;
+  int small_limit;
+};
+constexpr BSched kDefaultSched{8, 64 * 1024};
+constexpr int kCsCandidates[] = {4, 8, 16};
+constexpr int kSmallCandidates[] = {0, 32 * 1024, 64 * 1024};
+constexpr int kTuneMinWalks = 16;
+
+struct BTuneKey {
+  int device, n0, precs, nbucket, cbucket;
+  bool operator<(const BTuneKey& o) const {
+    if (device != o.device) return device < o.device;
+    if (n0 != o.n0) return n0 < o.n0;
+    if (precs != o.precs) return precs < o.precs;
+    if (nbucket != o.nbucket) return nbucket < o.nbucket;
+    return cbucket < o.cbucket;
+  }
+};
+
+std::mutex g_btune_mu;
+std::map<BTuneKey, BSched> g_btune;
+std::atomic<long long> g_btune_measurements{0};
+
+int ilog2(int v) {
+  int b = 0;
+  while (v > 1) {
+    v >>= 1;
+    ++b;
+  }
+  return b;
+}
+
+bool btune_lookup(const BTuneKey& k, BSched* out) {
+  std::lock_guard<std::mutex> lock(g_btune_mu);
+  auto it = g_btune.find(k);
+  if (it == g_btune.end()) return false;
+  *out = it->second;
+  return true;
+}
+
+BSched btune_store(const BTuneKey& k, const BSched& s) {
+  g_btune_measurements.fetch_add(1, std::memory_order_relaxed);
+  std::lock_guard<std::mutex> lock(g_btune_mu);
+  return g_btune.emplace(k, s).first->second;   // a concurrent tuner may have won
+}
+
+// Resident clusters of cs CTAs of the series-phase kernel (0: cannot run);
+// clusters of more than 8 CTAs are opted into on first use.
+int series_clusters(int device, int cs) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({device, cs});
+  if (it != cache.end()) return it->second;
+  if (cs > 8)
+    QSW_CUDA_TRY(cudaFuncSetAttribute(batch_series_kernel,
+                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)(cs * 4096));
+  cfg.blockDim = dim3(kBT);
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  int n = 0;
+  if (cudaOccupancyMaxActiveClusters(&n, batch_series_kernel, &cfg) != cudaSuccess) {
+    (void)cudaGetLastError();
+    n = 0;
+  }
+  cache[{device, cs}] = n;
+  return n;
+}
+
 }  // namespace
+
+long long batch_tune_measurements() { return g_btune_measurements.load(); }
+
+void batch_tune_reset() {
+  std::lock_guard<std::mutex> lock(g_btune_mu);
+  g_btune.clear();
+}
 
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,
@@ -981,12 +1150,13 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     cfg.gridDim = dim3(kCl * 4096);
     cfg.blockDim = dim3(kBT);
     cfg.numAttrs = 0;   // the kernel declares its cluster shape
-    QSW_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, batch_series_kernel, &cfg));
+    QSW_CUDA_TRY(cudaOccupancyMaxActiveClusters(&max_clusters, batch_norms_kernel, &cfg));
   }
   const int clusters = std::max(1, std::min(max_clusters, count));
-  cudaEvent_t e0, e1, e2;
+  cudaEvent_t e0, e1, e1b, e2;
   QSW_CUDA_TRY(cudaEventCreate(&e0));
   QSW_CUDA_TRY(cudaEventCreate(&e1));
+  QSW_CUDA_TRY(cudaEventCreate(&e1b));
   QSW_CUDA_TRY(cudaEventCreate(&e2));
   QSW_CUDA_TRY(cudaEventRecord(e0, st));
   QSW_LAUNCH batch_norms_kernel<<<clusters * kCl, kBT, 0, st>>>(args);
@@ -997,8 +1167,10 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   QSW_CUDA_TRY(cudaMemcpyAsync(dps.data(), dpbuf.p, sizeof(double) * dps.size(),
                                cudaMemcpyDeviceToHost, st));
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
-  std::vector<char> is_small(count, 0);
-  std::vector<size_t> smem_of(count, 0);
+  // Every walk gets Taylor-term blocks and an output ring in global memory,
+  // whichever schedule runs it (a walk small enough for one CTA needs a few KB).
+  std::vector<size_t> kbw(count), rbw(count);
+  int maxN = 0, precs = 0;
   for (int w = 0; w < count; ++w) {
     BWalk& W = hw[w];
     const double* theta = theta_table(W.f32 ? QSW_C64_BULK : QSW_C128);
@@ -1007,72 +1179,134 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
     W.njobs = info.njobs;
     W.ring = info.max_d + 1;
     const size_t vb = W.f32 ? sizeof(float2) : sizeof(double2);
-    const size_t kb = 2 * vb * n0 * (size_t)W.n;
-    const size_t rb = sizeof(double2) * (size_t)W.ring * n0 * W.n;
-    is_small[w] = kb <= kSmallKBytes;
-    W.fsmem = is_small[w] && kb + rb <= kSmallTotalBytes;
-    smem_of[w] = kb + (W.fsmem ? rb : 0);
-    if (!is_small[w]) {   // small walks keep their Taylor terms in shared memory
-      bufs.emplace_back();
-      bufs.back().alloc(2 * vb * n0 * (size_t)W.n);
-      W.kbuf = bufs.back().p;
-    }
-    if (!W.fsmem) {
-      bufs.emplace_back();
-      bufs.back().alloc(rb);
-      W.fring = bufs.back().as<double2>();
-    }
+    kbw[w] = 2 * vb * n0 * (size_t)W.n;
+    rbw[w] = sizeof(double2) * (size_t)W.ring * n0 * W.n;
+    bufs.emplace_back();
+    bufs.back().alloc(kbw[w]);
+    W.kbuf = bufs.back().p;
+    bufs.emplace_back();
+    bufs.back().alloc(rbw[w]);
+    W.fring = bufs.back().as<double2>();
     bufs.emplace_back();
     bufs.back().alloc(sizeof(Job) * std::max(1, W.njobs));
     W.jobs = bufs.back().as<Job>();
+    maxN = std::max(maxN, W.Nt);
+    precs |= W.f32 ? 2 : 1;
   }
-  std::vector<int> big, small;
-  size_t small_bytes = 0;
-  for (int w : order) {
-    if (is_small[w]) {
-      small.push_back(w);
-      small_bytes = std::max(small_bytes, smem_of[w]);
-    } else {
-      big.push_back(w);
-    }
-  }
-  QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice, st));
-  std::vector<int> lists(big);
-  lists.insert(lists.end(), small.begin(), small.end());
-  if (!lists.empty())
-    QSW_CUDA_TRY(cudaMemcpyAsync(dorder.as<int>() + count, lists.data(), sizeof(int) * lists.size(),
-                                 cudaMemcpyHostToDevice, st));
-  args.big = dorder.as<int>() + count;
-  args.nbig = (int)big.size();
-  args.small = args.big + big.size();
-  args.nsmall = (int)small.size();
-  const int clusters2 = std::max(1, std::min(max_clusters, (int)big.size()));
-  // small walks: one CTA each on the side stream, alongside the clusters
+  // One series phase under schedule sc: walks whose two Taylor-term blocks fit
+  // in sc.small_limit bytes run on one CTA each (terms in shared memory, and
+  // the ring too when both fit in kSmallTotalBytes) on the side stream; the
+  // others on clusters of sc.cs CTAs.  Returns the clusters launched.
+  std::vector<int> big, small, lists;
   cudaEvent_t fork = nullptr, join = nullptr;
-  if (!small.empty()) {
-    const int dyn = (int)small_bytes;
-    allow_small_smem(ctx->device);
-    int per_sm = 0;
-    QSW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_small_kernel, kBT, dyn));
-    const int grid = std::max(1, std::min((int)small.size(), std::max(1, per_sm) * ctx->num_sms));
-    cudaStream_t ss = st;
-    if (!big.empty()) {
-      if (!ctx->side) QSW_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-      QSW_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-      QSW_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
-      QSW_CUDA_TRY(cudaEventRecord(fork, st));
-      QSW_CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0));
-      ss = ctx->side;
+  auto phase2 = [&](const BSched& sc, bool with_sink) -> int {
+    big.clear();
+    small.clear();
+    size_t small_bytes = 0;
+    for (int w : order) {
+      BWalk& W = hw[w];
+      const bool sm = kbw[w] <= (size_t)sc.small_limit;
+      W.fsmem = sm && kbw[w] + rbw[w] <= kSmallTotalBytes;
+      W.done = (with_sink && sink) ? sink->d_done + w : nullptr;
+      if (sm) {
+        small.push_back(w);
+        small_bytes = std::max(small_bytes, kbw[w] + (W.fsmem ? rbw[w] : 0));
+      } else {
+        big.push_back(w);
+      }
     }
-    QSW_LAUNCH batch_small_kernel<<<grid, kBT, dyn, ss>>>(args);
-    QSW_CUDA_TRY(cudaGetLastError());
-    if (join) QSW_CUDA_TRY(cudaEventRecord(join, ss));
+    QSW_CUDA_TRY(cudaMemcpyAsync(dwalks.p, hw.data(), sizeof(BWalk) * count, cudaMemcpyHostToDevice,
+                                 st));
+    lists = big;
+    lists.insert(lists.end(), small.begin(), small.end());
+    if (!lists.empty())
+      QSW_CUDA_TRY(cudaMemcpyAsync(dorder.as<int>() + count, lists.data(), sizeof(int) * lists.size(),
+                                   cudaMemcpyHostToDevice, st));
+    QSW_CUDA_TRY(cudaMemsetAsync(dq.as<unsigned>() + 1, 0, 2 * sizeof(unsigned), st));
+    args.big = dorder.as<int>() + count;
+    args.nbig = (int)big.size();
+    args.small = args.big + big.size();
+    args.nsmall = (int)small.size();
+    if (!small.empty()) {
+      const int dyn = (int)small_bytes;
+      allow_small_smem(ctx->device);
+      int per_sm = 0;
+      QSW_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_small_kernel, kBT, dyn));
+      const int grid = std::max(1, std::min((int)small.size(), std::max(1, per_sm) * ctx->num_sms));
+      cudaStream_t ss = st;
+      if (!big.empty()) {
+        if (!ctx->side) QSW_CUDA_TRY(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+        if (!fork) QSW_CUDA_TRY(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+        if (!join) QSW_CUDA_TRY(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        QSW_CUDA_TRY(cudaEventRecord(fork, st));
+        QSW_CUDA_TRY(cudaStreamWaitEvent(ctx->side, fork, 0));
+        ss = ctx->side;
+      }
+      QSW_LAUNCH batch_small_kernel<<<grid, kBT, dyn, ss>>>(args);
+      QSW_CUDA_TRY(cudaGetLastError());
+      if (ss != st) QSW_CUDA_TRY(cudaEventRecord(join, ss));
+    }
+    int launched = 0;
+    if (!big.empty()) {
+      launched = std::max(1, std::min(series_clusters(ctx->device, sc.cs), (int)big.size()));
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = (unsigned)sc.cs;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3((unsigned)(launched * sc.cs));
+      cfg.blockDim = dim3(kBT);
+      cfg.dynamicSmemBytes = 0;
+      cfg.stream = st;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      QSW_CUDA_TRY((QSW_LAUNCH cudaLaunchKernelEx(&cfg, batch_series_kernel, args)));
+      // the small walks' kernel (side stream) runs alongside; the call's
+      // stream waits for both
+      if (!small.empty()) QSW_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
+    }
+    return launched;
+  };
+  // the schedule: the context's fixed one, the tuned one for this batch's
+  // kind, or (first batch of its kind) every candidate timed on this batch
+  BSched sc = kDefaultSched;
+  bool tuned = false;
+  const BTuneKey key{ctx->device, n0, precs, ilog2(maxN), ilog2(count)};
+  if (ctx->batch_cs > 0 || ctx->batch_small >= 0) {
+    if (count >= kTuneMinWalks) btune_lookup(key, &sc);   // the other half, when tuned
+    if (ctx->batch_cs > 0) sc.cs = ctx->batch_cs;
+    if (ctx->batch_small >= 0) sc.small_limit = ctx->batch_small;
+  } else if (count >= kTuneMinWalks) {
+    if (!btune_lookup(key, &sc) && !ctx->batch_no_tune) {
+      cudaEvent_t ta, tb;
+      QSW_CUDA_TRY(cudaEventCreate(&ta));
+      QSW_CUDA_TRY(cudaEventCreate(&tb));
+      float best_ms = 0.f;
+      for (int cs : kCsCandidates) {
+        if (series_clusters(ctx->device, cs) < 1) continue;
+        for (int sl : kSmallCandidates) {
+          const BSched cand{cs, sl};
+          QSW_CUDA_TRY(cudaEventRecord(ta, st));
+          phase2(cand, false);
+          QSW_CUDA_TRY(cudaEventRecord(tb, st));
+          QSW_CUDA_TRY(cudaEventSynchronize(tb));
+          float ms = 0.f;
+          QSW_CUDA_TRY(cudaEventElapsedTime(&ms, ta, tb));
+          if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            sc = cand;
+          }
+        }
+      }
+      cudaEventDestroy(ta);
+      cudaEventDestroy(tb);
+      sc = btune_store(key, sc);
+      tuned = true;
+    }
   }
-  if (!big.empty()) {
-    QSW_LAUNCH batch_series_kernel<<<clusters2 * kCl, kBT, 0, st>>>(args);
-    QSW_CUDA_TRY(cudaGetLastError());
-  }
-  if (join) QSW_CUDA_TRY(cudaStreamWaitEvent(st, join, 0));
+  QSW_CUDA_TRY(cudaEventRecord(e1b, st));
+  const int clusters2 = phase2(sc, true);
   QSW_CUDA_TRY(cudaEventRecord(e2, st));
   if (sink) {
     // hand finished walks out while the kernels run; the loop ends when both
@@ -1094,9 +1328,10 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
   float ms1 = 0, ms2 = 0;
   cudaEventElapsedTime(&ms1, e0, e1);
-  cudaEventElapsedTime(&ms2, e1, e2);
+  cudaEventElapsedTime(&ms2, e1b, e2);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(e1b);
   cudaEventDestroy(e2);
   if (fork) cudaEventDestroy(fork);
   if (join) cudaEventDestroy(join);
@@ -1105,6 +1340,9 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   if (stats) {
     stats->walks = count;
     stats->clusters = big.empty() ? 0 : clusters2;
+    stats->cluster_size = sc.cs;
+    stats->small_limit = sc.small_limit;
+    stats->tuned = tuned ? 1 : 0;
     stats->small_walks = (int)small.size();
     stats->norms_ms = ms1;
     stats->series_ms = ms2;

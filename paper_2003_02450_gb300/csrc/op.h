@@ -14,6 +14,9 @@ struct qsw_ctx {
   int* count_h = nullptr;        // owned, host-mapped: final-output counter of a series
   int* count_d = nullptr;        // its device address
   int num_sms = 0;
+  int batch_cs = 0;        // qsw_batch_set_schedule: CTAs per cluster (0: tuned)
+  int batch_small = -1;    // ... and the one-CTA limit in bytes (-1: tuned)
+  bool batch_no_tune = false;   // use tuned schedules, never time candidates (server workers)
   std::string last_error;
 };
 
@@ -182,6 +185,8 @@ struct WalkSink {
 void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_rho0, int n0,
                const double* t0s, const double* dts, const int* steps, double* const* d_pops,
                qsw_batch_stats* stats, const WalkSink* sink = nullptr);
+long long batch_tune_measurements();   // series-phase schedules measured in this process
+void batch_tune_reset();               // forget every tuned series-phase schedule
 // est.cu
 void run_survival(Op& op, const double* d_rho0, double t_end, int q, int sink, double* eta,
                   double* d_pops, qsw_series_stats* stats);

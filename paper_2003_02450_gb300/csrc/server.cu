@@ -16,6 +16,10 @@
 // device memory is released in stream order when its launch ends (and only then
 // counted free for admission), so no worker ever synchronises the whole device.
 //
+// Workers take the batched series phase's schedule from the tuner's cache
+// (filled by earlier qsw_batch_series calls) and never time candidates
+// themselves, so no request waits for a tuning pass.
+//
 // A walk's result does not depend on the other walks of its batch: each walk
 // is computed by its own cluster with its own reductions in a fixed order, so a
 // request gives the same populations alone and in any mix.
@@ -331,6 +335,7 @@ qsw_status qsw_server_create(int device, const qsw_server_config* cfg, qsw_serve
     qsw_ctx* c = nullptr;
     const qsw_status r = qsw_create(&c, device, st);
     if (r != QSW_OK) return r;
+    c->batch_no_tune = true;   // a worker never stalls a batch to time schedules
     s->ctxs.push_back(c);
   }
   for (int k = 0; k < s->workers; ++k) s->threads.emplace_back(&qsw_server::worker, s.get(), k);

@@ -69,7 +69,8 @@ class qsw_batch_stats(ctypes.Structure):
     _fields_ = [("walks", c_int32), ("clusters", c_int32), ("norms_ms", c_double),
                 ("series_ms", c_double), ("matvecs", c_int64), ("fupdates", c_int64),
                 ("small_walks", c_int32), ("algorithmic_flops", c_double),
-                ("algorithmic_bytes", c_double)]
+                ("algorithmic_bytes", c_double), ("cluster_size", c_int32),
+                ("small_limit", c_int32), ("tuned", c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -139,6 +140,7 @@ _SIGNATURES = {
     "qsw_device_allocations": ([], c_int64),
     "qsw_tune_measurements": ([], c_int64),
     "qsw_tune_reset": ([], None),
+    "qsw_batch_set_schedule": ([c_void_p, c_int32, c_int32], c_int32),
     "qsw_op_schedule": ([c_void_p, POINTER(c_int32), POINTER(c_int32)], c_int32),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
     "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
@@ -498,6 +500,11 @@ def qsw_tune_measurements() -> int:
 
 def qsw_tune_reset() -> None:
     lib().qsw_tune_reset()
+
+
+def qsw_batch_set_schedule(ctx, cluster_size: int = 0, small_limit: int = -1) -> None:
+    """Fix the batched series phase's schedule for this context (0 / -1: tuned)."""
+    _check(lib().qsw_batch_set_schedule(ctx, int(cluster_size), int(small_limit)), ctx)
 
 
 def qsw_op_schedule(op, with_unroll: bool = False):
