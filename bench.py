@@ -951,7 +951,7 @@ def run_serve_workload(args):
     """Request stream: ER digraphs with mean out-degree 8, N log-uniform in
     [32, 1024], omega ~ U(0,1), 1..100 output times of dt = 0.1, complex64 /
     complex128 50/50, rho0 = |0><0|.  First the capacity (all requests submitted
-    at once), then Poisson arrivals at 0.5x and 0.9x that capacity; latency =
+    at once), then Poisson arrivals at 0.5x and 0.9x that capacity and at a fixed 60 requests/s; latency =
     submit -> populations on the host."""
     import threading
     import numpy as np
@@ -999,6 +999,8 @@ def run_serve_workload(args):
     loads = {}
     for load in (0.5, 0.9):
         loads[str(load)] = run(load * cap["throughput_rps"])
+    # one fixed absolute rate, so that runs with different capacities compare
+    loads["60rps"] = run(60.0)
     cpu = None
     if not args.no_cpu_baseline:
         try:
