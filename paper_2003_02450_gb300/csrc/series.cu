@@ -61,16 +61,20 @@ enum : int { kErrNone = 0, kErrBarrier = 1, kErrPlan = 2 };
 enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2, kOpGlobal = 3, kOpGlobalHerm = 4 };
 static_assert(kItemRows == 32 * kRpt, "a work item is one row per lane per kRpt");
 
+// Each group of words that the grid hits at once sits in its own 256-byte
+// block: the barrier's arrival counter, the word it spins on, the item
+// counters and the norm maxima (sharing lines made the atomics and the spin
+// reads of one barrier queue behind each other: 1 % of the ER-1000 series).
 struct Ctrl {
-  unsigned int bar_count;
-  unsigned int bar_gen;
-  int error;
+  alignas(256) unsigned int bar_count;
+  alignas(256) unsigned int bar_gen;
+  alignas(256) int error;
   int njobs;
   unsigned long long matvecs;
   unsigned long long fupdates;   // sum over terms of the outputs updated
-  unsigned int work[3];          // matrix-free column counters, one per term slot
-  unsigned int work2[3];         // global walks: pass-A counters
-  unsigned long long gmax[3][1 + kDMax];
+  alignas(256) unsigned int work[3];    // matrix-free column counters, one per term slot
+  alignas(256) unsigned int work2[3];   // global walks: pass-A counters
+  alignas(256) unsigned long long gmax[3][1 + kDMax];
 };
 
 struct SeriesArgs {
