@@ -105,8 +105,8 @@ struct BArgs {
   double tol[2];
 };
 
-constexpr size_t kSmallKBytes = 64 * 1024;       // two Taylor-term blocks of a small walk
-constexpr size_t kSmallTotalBytes = 96 * 1024;   // ... plus its output ring, when that fits
+constexpr size_t kSmallTotalBytes = 96 * 1024;   // a small walk's two Taylor-term blocks plus
+                                                 // its output ring, when both fit on chip
 
 __device__ __forceinline__ unsigned long long bits_of(double v) {
   return (unsigned long long)__double_as_longlong(v);
@@ -903,7 +903,9 @@ batch_series_kernel(BArgs a) {
 }
 
 // Phase 2 for small walks: one CTA per walk, Taylor terms in dynamic shared
-// memory (2 n0 n values of the walk's precision, at most kSmallKBytes).
+// memory (2 n0 n values of the walk's precision, at most the schedule's
+// one-CTA limit).  CTAs of 128 threads measured the same on the EST sweep
+// and 64 or 32 threads slower (a walk's term then runs on fewer warps).
 __global__ void __launch_bounds__(kBT) batch_small_kernel(BArgs a) {
   extern __shared__ __align__(16) unsigned char s_k[];
   __shared__ Red R;
