@@ -536,17 +536,21 @@ int64_t qsw_device_allocations(void);
  * Not in the paper (a schedule choice of this library).  The CSR sweep of
  * the series kernel runs TPR lanes per row of L~ (1, 2, 4, 8, 16 or 32), which
  * sets the cost of its shuffle reductions and how the operator stream is
- * coalesced, and keeps 2 or 4 entries per lane in flight (unroll depth).
+ * coalesced, or the sliced form (qsw_op_schedule), and keeps 2 or 4 entries
+ * per lane in flight (unroll depth).
  * The first qsw_expmv_series on a QSW_OPERATOR_CSR operator
  * (without QSW_BUILD_FIXED_SCHEDULE) looks up the device's choice for its
  * (precision, row-length bucket, size bucket); when there is none it times
  * every candidate pair with the series kernel on that operator (eight Taylor
- * terms from a fixed vector, 36 short launches, plus two Taylor-term vectors
- * of workspace), keeps the fastest for the life of the process and uses it
- * for every later operator in that bucket.  Results depend on the choice
- * only through the summation order within a row (well inside the 1e-10
- * parity bound).  The no-allocation entry point never tunes: it uses the
- * operator's current value. */
+ * terms from a fixed vector, 42 short launches, plus two Taylor-term vectors
+ * of workspace and the sliced copy of the operator, which is kept only when
+ * the sliced form wins), keeps the fastest for the life of the process and
+ * uses it for every later operator in that bucket.  Results depend on the
+ * choice only through the summation order within a row (well inside the
+ * 1e-10 parity bound).  The no-allocation entry point never tunes: it uses
+ * the operator's current value, and the sliced form only when its copy is
+ * already built (after qsw_set_omega, the first qsw_expmv_series rebuilds
+ * it; until then the no-allocation call runs the lanes-per-row form). */
 
 /* Number of schedule measurements (one per tuned CSR bucket, and one per
  * tuned kind of batch: qsw_batch_set_schedule) made in this process.  Pure
@@ -558,9 +562,17 @@ int64_t qsw_tune_measurements(void);
 void qsw_tune_reset(void);
 /* The operator's CSR schedule (0 and 0 for a matrix-free operator): lanes
  * per row and the row loop's unroll depth (2 or 4 entries per lane in flight;
- * csr_unroll may be NULL).  The heuristic values until its first series, the
- * tuned values after it. */
+ * csr_unroll may be NULL).  lanes per row -1: the sliced form (one lane per
+ * row, the operator copied into 32-row slices sorted by row length within
+ * windows of 4096 rows, so that a warp's loads of the operator are
+ * contiguous; it holds a second copy of the operator's entries, padded).
+ * The heuristic values until its first series, the tuned values after it. */
 qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row, int32_t* csr_unroll);
+/* Fix a QSW_OPERATOR_CSR operator's schedule (no tuning for it afterwards):
+ * csr_lanes_per_row 1, 2, 4, 8, 16, 32 or -1 (the sliced form, built by the
+ * next qsw_expmv_series), csr_unroll 2 or 4.  Pure host call.
+ * Errors: INVALID_ARG (a matrix-free operator, or another value). */
+qsw_status qsw_op_set_csr_schedule(qsw_op* op, int32_t csr_lanes_per_row, int32_t csr_unroll);
 
 /* theta_m for m = 1..55 of the given precision (tol 2^-53 or 2^-24): the
  * largest theta with sum_{k>m} |c_k| theta^(k-1) <= tol, c_k the Taylor

@@ -191,6 +191,7 @@ void rebuild(Op& op, bool defer_norms) {
   qsw::build_jumps(op);
   qsw::prep_matfree(op);
   op.L = qsw::Csr{};
+  op.sell = qsw::Sell{};   // its values follow L: rebuilt by the next series that uses it
   op.norms_ready = !defer_norms;
   if (op.opkind == QSW_OPERATOR_CSR) {
     qsw::Csr LH;
@@ -726,11 +727,30 @@ qsw_status qsw_batch_set_schedule(qsw_ctx* ctx, int32_t cluster_size, int32_t sm
   });
 }
 
+qsw_status qsw_op_set_csr_schedule(qsw_op* h, int32_t csr_lanes_per_row, int32_t csr_unroll) {
+  Op* op = reinterpret_cast<Op*>(h);
+  return guarded(op ? op->ctx : nullptr, [&] {
+    QSW_CHECK_ARG(op != nullptr && op->opkind == QSW_OPERATOR_CSR, QSW_ERR_INVALID_ARG,
+                  "a CSR operator is required");
+    const int l = csr_lanes_per_row;
+    QSW_CHECK_ARG(l == -1 || l == 1 || l == 2 || l == 4 || l == 8 || l == 16 || l == 32,
+                  QSW_ERR_INVALID_ARG, "csr_lanes_per_row must be -1, 1, 2, 4, 8, 16 or 32");
+    QSW_CHECK_ARG(csr_unroll == 2 || csr_unroll == 4, QSW_ERR_INVALID_ARG, "csr_unroll must be 2 or 4");
+    op->tpr_fixed = true;
+    op->csr_sell = l < 0;
+    if (l > 0) {
+      op->tpr = l;
+      op->sell = qsw::Sell{};
+    }
+    op->csr_unroll = csr_unroll;
+  });
+}
+
 qsw_status qsw_op_schedule(const qsw_op* op, int32_t* csr_lanes_per_row, int32_t* csr_unroll) {
   if (!op || !csr_lanes_per_row) return QSW_ERR_INVALID_ARG;
   const Op* o = reinterpret_cast<const Op*>(op);
   const bool csr = o->opkind == QSW_OPERATOR_CSR;
-  *csr_lanes_per_row = csr ? o->tpr : 0;
+  *csr_lanes_per_row = csr ? (o->csr_sell ? -1 : o->tpr) : 0;
   if (csr_unroll) *csr_unroll = csr ? o->csr_unroll : 0;
   return QSW_OK;
 }

@@ -48,6 +48,21 @@ struct Csr {
   bool fp32 = false;
 };
 
+// The CSR operator in 32-row slices (sliced ELLPACK, SELL-32-sigma): rows
+// sorted by length, longest first, within windows of kSellSigma rows; slice s
+// holds rows perm[32 s .. 32 s + 31] column-major (entry k of the slice's
+// lane l at off[s] + 32 k + l), each row padded to the slice's width with
+// zero values (column: the row itself).  One lane per row, and a warp's
+// loads of the operator stream are contiguous.
+struct Sell {
+  DevBuf col, val;          // [entries]: int, and the CSR's value type
+  DevBuf perm;              // [32 slices]: row of each lane, -1 past n
+  DevBuf off;               // [slices]: int64 offset of each slice
+  DevBuf width;             // [slices]: entries per lane
+  long long entries = 0;    // padded
+  int slices = 0;
+};
+
 // Coefficients of the matrix-free operator (matfree.cuh), FP64 and FP32 copies.
 struct MfData {
   DevBuf hval64, hval32;   // (1 - omega) H_offdiag
@@ -116,6 +131,8 @@ struct Op {
   int tpr = 8;     // SpMV threads per row
   int csr_unroll = 2;       // CSR sweep: entries per lane in flight (2 or 4)
   bool tpr_fixed = false;   // set: keep tpr and csr_unroll (tuned, or QSW_BUILD_FIXED_SCHEDULE)
+  bool csr_sell = false;    // the tuned CSR schedule is the sliced form (sell), not TPR lanes
+  Sell sell;                // built when csr_sell (values follow set_omega: rebuilt on use)
   bool norms_ready = false;
   bool rank64 = false;      // QSW_BUILD_FP64_RANKING: the estimator's adjoint step in FP64
 
@@ -170,6 +187,7 @@ void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y
 void mf_apply32(const Op& op, bool adjoint, int cols, const float* x, float* y, double scale);
 int choose_tpr(double avg_row);
 void tune_csr_schedule(Op& op);  // autotuned lanes per row and unroll (cached per bucket)
+void build_sell(Op& op);         // op.sell from op.L (allocates)
 long long tune_measurements();   // schedule measurements made in this process
 void tune_reset();               // forget every tuned schedule
 // batch.cu

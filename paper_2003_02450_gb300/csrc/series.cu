@@ -58,7 +58,8 @@ constexpr int kRpt = 2;                 // rows per thread in one matrix-free pa
 constexpr unsigned kSpinLimit = 1u << 24;  // bounded barrier wait (~seconds)
 
 enum : int { kErrNone = 0, kErrBarrier = 1, kErrPlan = 2 };
-enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2, kOpGlobal = 3, kOpGlobalHerm = 4 };
+enum : int { kOpCsr = 0, kOpMatfree = 1, kOpMatfreeHerm = 2, kOpGlobal = 3, kOpGlobalHerm = 4,
+             kOpSell = 5 };
 static_assert(kItemRows == 32 * kRpt, "a work item is one row per lane per kRpt");
 
 // Each group of words that the grid hits at once sits in its own 256-byte
@@ -79,9 +80,13 @@ struct Ctrl {
 
 struct SeriesArgs {
   int n, nt;
-  const int* rowptr;     // CSR operator
+  const int* rowptr;     // CSR operator (col and val: its slices, for the sliced form)
   const int* col;
   const void* val;
+  const int* sperm;      // sliced form: row of each lane, slice offsets and widths
+  const long long* soff;
+  const int* swidth;
+  int slices;
   MfOp<double> mf64;     // matrix-free operator (one of the two is used)
   MfOp<float> mf32;
   GqOp<double> gq64;     // global-interaction walk (one of the two is used)
@@ -401,7 +406,7 @@ series_kernel(SeriesArgs a) {
             if (kHerm && i != j) knext[j + (long long)nt * i] = Cplx<VT>::conj_of(yx, yy);
           }
         }
-      } else if (OPK != kOpCsr) {
+      } else if (OPK == kOpMatfree || OPK == kOpMatfreeHerm) {
         // ---- matrix-free sweep: warps take 64-row chunks of columns from a
         // counter (no block-level synchronisation inside the pass)
         constexpr bool kHerm = OPK == kOpMatfreeHerm;
@@ -430,6 +435,63 @@ series_kernel(SeriesArgs a) {
             if (kHerm && irow[u] != j)
               knext[j + (long long)nt * irow[u]] = Cplx<VT>::conj_of(yx, yy);
           }
+        }
+      } else if (OPK == kOpSell) {
+        // ---- sliced CSR sweep: one lane per row, a warp per 32-row slice;
+        // entry k of every lane of a slice is one contiguous 32-entry load
+        const VT* __restrict__ val = static_cast<const VT*>(a.val);
+        const int* __restrict__ col = a.col;
+        const long long wglobal = gthread / 32;
+        const long long wstride = (long long)gridDim.x * kWarps;
+        for (long long sl = wglobal; sl < a.slices; sl += wstride) {
+          const int r = a.sperm[sl * 32 + lane];
+          const long long base = a.soff[sl] + lane;
+          const int w = a.swidth[sl];
+          R ax = 0, ay = 0, bx = 0, by = 0;
+          int k = 0;
+          if (UNR == 4) {
+            R cx = 0, cy = 0, dx = 0, dy = 0;
+            for (; k + 3 < w; k += 4) {
+              const long long e = base + 32LL * k;
+              const int c0 = __ldcs(col + e), c1 = __ldcs(col + e + 32);
+              const int c2 = __ldcs(col + e + 64), c3 = __ldcs(col + e + 96);
+              const VT v0 = __ldcs(val + e), v1 = __ldcs(val + e + 32);
+              const VT v2 = __ldcs(val + e + 64), v3 = __ldcs(val + e + 96);
+              const VT x0 = __ldcg(kcur + c0), x1 = __ldcg(kcur + c1);
+              const VT x2 = __ldcg(kcur + c2), x3 = __ldcg(kcur + c3);
+              ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+              ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+              bx = fma(v1.x, x1.x, fma(-v1.y, x1.y, bx));
+              by = fma(v1.x, x1.y, fma(v1.y, x1.x, by));
+              cx = fma(v2.x, x2.x, fma(-v2.y, x2.y, cx));
+              cy = fma(v2.x, x2.y, fma(v2.y, x2.x, cy));
+              dx = fma(v3.x, x3.x, fma(-v3.y, x3.y, dx));
+              dy = fma(v3.x, x3.y, fma(v3.y, x3.x, dy));
+            }
+            ax += cx;
+            ay += cy;
+            bx += dx;
+            by += dy;
+          }
+          for (; k + 1 < w; k += 2) {
+            const long long e = base + 32LL * k;
+            const int c0 = __ldcs(col + e), c1 = __ldcs(col + e + 32);
+            const VT v0 = __ldcs(val + e), v1 = __ldcs(val + e + 32);
+            const VT x0 = __ldcg(kcur + c0), x1 = __ldcg(kcur + c1);
+            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+            bx = fma(v1.x, x1.x, fma(-v1.y, x1.y, bx));
+            by = fma(v1.x, x1.y, fma(v1.y, x1.x, by));
+          }
+          if (k < w) {
+            const long long e = base + 32LL * k;
+            const int c0 = __ldcs(col + e);
+            const VT v0 = __ldcs(val + e);
+            const VT x0 = __ldcg(kcur + c0);
+            ax = fma(v0.x, x0.x, fma(-v0.y, x0.y, ax));
+            ay = fma(v0.x, x0.y, fma(v0.y, x0.x, ay));
+          }
+          if (r >= 0) ep.consume(r, (ax + bx) * rscale, (ay + by) * rscale);
         }
       } else {
         // ---- CSR sweep: TPR lanes per row.  A warp owns 32 consecutive rows and
@@ -751,8 +813,9 @@ cudaError_t launch_series(const SeriesArgs& a, int sms, cudaStream_t st, int* gr
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorLaunchOutOfResources;
   const long long want =
-      OPK == kOpCsr ? ((long long)a.n + 32 * kWarps - 1) / (32 * kWarps)   // 32 rows per warp
-                    : (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps;
+      OPK == kOpCsr    ? ((long long)a.n + 32 * kWarps - 1) / (32 * kWarps)   // 32 rows per warp
+      : OPK == kOpSell ? ((long long)a.slices + kWarps - 1) / kWarps           // a slice per warp
+                       : (mf_item_count(a.nt, OPK == kOpMatfreeHerm) + kWarps - 1) / kWarps;
   const long long maxg = (long long)per_sm * sms;
   const int grid = (int)std::max<long long>(1, std::min(want, maxg));
   *grid_out = grid;
@@ -772,6 +835,9 @@ cudaError_t launch_series_op(const Op& op, int tpr, int unr, bool herm, const Se
   if (op.opkind == QSW_OPERATOR_MATRIX_FREE)
     return herm ? launch_series<VT, kOpMatfreeHerm, 1>(a, sms, st, g)
                 : launch_series<VT, kOpMatfree, 1>(a, sms, st, g);
+  if (tpr < 0)   // the sliced form (a.col, a.val and the slice arrays set by the caller)
+    return unr == 4 ? launch_series<VT, kOpSell, 1, 4>(a, sms, st, g)
+                    : launch_series<VT, kOpSell, 1, 2>(a, sms, st, g);
 #define QSW_CSR_CASE(T)                                                        \
   case T:                                                                      \
     return unr == 4 ? launch_series<VT, kOpCsr, T, 4>(a, sms, st, g)           \
@@ -848,13 +914,123 @@ void tune_reset() {
   g_tune_tpr.clear();
 }
 
+// ------------------------------------------------------- sliced CSR form
+namespace {
+
+constexpr int kSellSigma = 4096;   // rows sorted by length within windows of this many
+
+// Slice s, lane l: row perm[32 s + l] (-1: none), its CSR entries in order,
+// then zero entries pointing at the row itself up to the slice's width.
+template <class VT>
+__global__ void sell_fill_kernel(int slices, const int* __restrict__ perm,
+                                 const long long* __restrict__ off, const int* __restrict__ width,
+                                 const int* __restrict__ rowptr, const int* __restrict__ ccol,
+                                 const VT* __restrict__ cval, int* __restrict__ scol,
+                                 VT* __restrict__ sval) {
+  const int lane = threadIdx.x & 31;
+  const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long ws = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long sl = w0; sl < slices; sl += ws) {
+    const int r = perm[sl * 32 + lane];
+    const int e0 = r >= 0 ? rowptr[r] : 0;
+    const int len = r >= 0 ? rowptr[r + 1] - e0 : 0;
+    const int w = width[sl];
+    VT zero;
+    zero.x = 0;
+    zero.y = 0;
+    for (int k = 0; k < w; ++k) {
+      const long long e = off[sl] + 32LL * k + lane;
+      if (k < len) {
+        scol[e] = ccol[e0 + k];
+        sval[e] = cval[e0 + k];
+      } else {
+        scol[e] = r >= 0 ? r : 0;
+        sval[e] = zero;
+      }
+    }
+  }
+}
+
+}  // namespace
+
+void build_sell(Op& op) {
+  cudaStream_t st = op.ctx->stream;
+  const long long n = op.n;
+  std::vector<int> rp((size_t)n + 1);
+  QSW_CUDA_TRY(cudaMemcpyAsync(rp.data(), op.L.rowptr.p, sizeof(int) * (n + 1),
+                               cudaMemcpyDeviceToHost, st));
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));
+  Sell& S = op.sell;
+  S.slices = (int)((n + 31) / 32);
+  std::vector<int> perm((size_t)S.slices * 32, -1);
+  for (long long w0 = 0; w0 < n; w0 += kSellSigma) {
+    const long long w1 = std::min(n, w0 + kSellSigma);
+    for (long long r = w0; r < w1; ++r) perm[r] = (int)r;
+    std::stable_sort(perm.begin() + w0, perm.begin() + w1, [&](int x, int y) {
+      return rp[x + 1] - rp[x] > rp[y + 1] - rp[y];
+    });
+  }
+  std::vector<long long> off(S.slices);
+  std::vector<int> width(S.slices);
+  long long tot = 0;
+  for (int sl = 0; sl < S.slices; ++sl) {
+    int w = 0;
+    for (int l = 0; l < 32; ++l) {
+      const int r = perm[(size_t)sl * 32 + l];
+      if (r >= 0) w = std::max(w, rp[r + 1] - rp[r]);
+    }
+    off[sl] = tot;
+    width[sl] = w;
+    tot += 32LL * w;
+  }
+  S.entries = tot;
+  const size_t vb = op.L.fp32 ? sizeof(float2) : sizeof(double2);
+  S.perm.alloc(sizeof(int) * perm.size());
+  S.off.alloc(sizeof(long long) * off.size());
+  S.width.alloc(sizeof(int) * width.size());
+  S.col.alloc(sizeof(int) * (size_t)std::max(1LL, tot));
+  S.val.alloc(vb * (size_t)std::max(1LL, tot));
+  QSW_CUDA_TRY(cudaMemcpyAsync(S.perm.p, perm.data(), sizeof(int) * perm.size(),
+                               cudaMemcpyHostToDevice, st));
+  QSW_CUDA_TRY(cudaMemcpyAsync(S.off.p, off.data(), sizeof(long long) * off.size(),
+                               cudaMemcpyHostToDevice, st));
+  QSW_CUDA_TRY(cudaMemcpyAsync(S.width.p, width.data(), sizeof(int) * width.size(),
+                               cudaMemcpyHostToDevice, st));
+  const unsigned grid = grid_for((long long)S.slices * 32, 256, 152 * 16);
+  if (op.L.fp32)
+    QSW_LAUNCH sell_fill_kernel<float2><<<grid, 256, 0, st>>>(
+        S.slices, S.perm.as<int>(), S.off.as<long long>(), S.width.as<int>(),
+        op.L.rowptr.as<int>(), op.L.col.as<int>(), op.L.val.as<float2>(), S.col.as<int>(),
+        S.val.as<float2>());
+  else
+    QSW_LAUNCH sell_fill_kernel<double2><<<grid, 256, 0, st>>>(
+        S.slices, S.perm.as<int>(), S.off.as<long long>(), S.width.as<int>(),
+        op.L.rowptr.as<int>(), op.L.col.as<int>(), op.L.val.as<double2>(), S.col.as<int>(),
+        S.val.as<double2>());
+  QSW_CUDA_TRY(cudaGetLastError());
+  QSW_CUDA_TRY(cudaStreamSynchronize(st));   // the host arrays above are released on return
+}
+
+namespace {
+// Points a series' operator arguments at the sliced form.
+void set_sell_args(const Op& op, SeriesArgs& a) {
+  a.col = op.sell.col.as<int>();
+  a.val = op.sell.val.p;
+  a.sperm = op.sell.perm.as<int>();
+  a.soff = op.sell.off.as<long long>();
+  a.swidth = op.sell.width.as<int>();
+  a.slices = op.sell.slices;
+}
+}  // namespace
+
 void tune_csr_schedule(Op& op) {
   const TuneKey key = csr_tune_key(op);
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     auto it = g_tune_tpr.find(key);
     if (it != g_tune_tpr.end()) {
-      op.tpr = it->second.first;
+      op.csr_sell = it->second.first < 0;
+      if (!op.csr_sell) op.tpr = it->second.first;
       op.csr_unroll = it->second.second;
       return;
     }
@@ -896,15 +1072,23 @@ void tune_csr_schedule(Op& op) {
   QSW_CUDA_TRY(cudaEventCreate(&e1));
   std::pair<int, int> best{op.tpr, op.csr_unroll};
   float best_ms = 0.f;
-  for (int tpr : kTprCandidates)
+  // the candidates: TPR lanes per row on the CSR arrays, and the sliced form
+  // (lanes per row -1), each with both unroll depths
+  std::vector<int> tprs(std::begin(kTprCandidates), std::end(kTprCandidates));
+  tprs.push_back(-1);
+  if (op.sell.slices == 0) build_sell(op);
+  SeriesArgs as = a;
+  set_sell_args(op, as);
+  for (int tpr : tprs)
   for (int unr : kUnrollCandidates) {
+    const SeriesArgs& aa = tpr < 0 ? as : a;
     float tmin = 0.f;
     for (int rep = 0; rep < 3; ++rep) {
       QSW_CUDA_TRY(cudaMemsetAsync(ctrl.p, 0, sizeof(Ctrl), st));
       QSW_CUDA_TRY(cudaEventRecord(e0, st));
       int grid = 0;
-      QSW_CUDA_TRY(f32 ? launch_series_op<float2>(op, tpr, unr, false, a, op.ctx->num_sms, st, &grid)
-                       : launch_series_op<double2>(op, tpr, unr, false, a, op.ctx->num_sms, st, &grid));
+      QSW_CUDA_TRY(f32 ? launch_series_op<float2>(op, tpr, unr, false, aa, op.ctx->num_sms, st, &grid)
+                       : launch_series_op<double2>(op, tpr, unr, false, aa, op.ctx->num_sms, st, &grid));
       QSW_CUDA_TRY(cudaEventRecord(e1, st));
       QSW_CUDA_TRY(cudaEventSynchronize(e1));
       float ms = 0.f;
@@ -926,7 +1110,11 @@ void tune_csr_schedule(Op& op) {
   g_tune_measurements.fetch_add(1, std::memory_order_relaxed);
   std::lock_guard<std::mutex> lock(g_tune_mu);
   const auto chosen = g_tune_tpr.emplace(key, best).first->second;   // a concurrent tuner may have won
-  op.tpr = chosen.first;
+  op.csr_sell = chosen.first < 0;
+  if (!op.csr_sell) {
+    op.tpr = chosen.first;
+    op.sell = Sell{};   // the sliced copy of the operator is not kept
+  }
   op.csr_unroll = chosen.second;
 }
 
@@ -1070,6 +1258,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
     tune_csr_schedule(op);
     op.tpr_fixed = true;
   }
+  if (op.opkind == QSW_OPERATOR_CSR && op.csr_sell && op.sell.slices == 0) build_sell(op);
   op.kbuf.alloc(2 * vbytes * (size_t)op.n);
   if (!d_out) op.ring.alloc(sizeof(double2) * (size_t)op.n * ring);
   op.jobs.alloc(sizeof(Job) * std::max(1, info.njobs));
@@ -1103,10 +1292,12 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   a.n = (int)op.n;
   a.nt = op.Nt;
   a.mirror = herm && d_out != nullptr;
+  const bool sell = op.opkind == QSW_OPERATOR_CSR && op.csr_sell && op.sell.slices > 0;
   if (op.opkind == QSW_OPERATOR_CSR) {
     a.rowptr = op.L.rowptr.as<int>();
     a.col = op.L.col.as<int>();
     a.val = op.L.val.p;
+    if (sell) set_sell_args(op, a);
   } else if (op.gq.active) {
     a.gq64 = make_gq<double>(op, false);
     a.gq32 = make_gq<float>(op, false);
@@ -1133,8 +1324,9 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   QSW_CUDA_TRY(cudaEventCreate(&ev1));
   QSW_CUDA_TRY(cudaEventRecord(ev0, st));
   int grid = 0;
-  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
-                      : launch_series_op<double2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
+  const int tpr = sell ? -1 : op.tpr;
+  cudaError_t e = f32 ? launch_series_op<float2>(op, tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
   QSW_CUDA_TRY(e);
   QSW_CUDA_TRY(cudaEventRecord(ev1, st));
   Ctrl h{};
@@ -1260,10 +1452,13 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
   a.n = (int)op.n;
   a.nt = op.Nt;
   a.mirror = herm && d_out != nullptr;
+  // the sliced form only when it is already built (this path allocates nothing)
+  const bool sell = op.opkind == QSW_OPERATOR_CSR && op.csr_sell && op.sell.slices > 0;
   if (op.opkind == QSW_OPERATOR_CSR) {
     a.rowptr = op.L.rowptr.as<int>();
     a.col = op.L.col.as<int>();
     a.val = op.L.val.p;
+    if (sell) set_sell_args(op, a);
   } else {
     a.mf64 = make_mf<double>(op, false);
     a.mf32 = make_mf<float>(op, false);
@@ -1280,8 +1475,9 @@ void run_series_noalloc(Op& op, const double* d_rho0, double t0, double dt, int 
   a.tol = tolerance(op.precision);
 
   int grid = 0;
-  cudaError_t e = f32 ? launch_series_op<float2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
-                      : launch_series_op<double2>(op, op.tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
+  const int tpr = sell ? -1 : op.tpr;
+  cudaError_t e = f32 ? launch_series_op<float2>(op, tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid)
+                      : launch_series_op<double2>(op, tpr, op.csr_unroll, herm, a, op.ctx->num_sms, st, &grid);
   QSW_CUDA_TRY(e);
   Ctrl h{};
   QSW_CUDA_TRY(cudaMemcpyAsync(&h, ctrl, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));

@@ -141,6 +141,7 @@ _SIGNATURES = {
     "qsw_tune_measurements": ([], c_int64),
     "qsw_tune_reset": ([], None),
     "qsw_batch_set_schedule": ([c_void_p, c_int32, c_int32], c_int32),
+    "qsw_op_set_csr_schedule": ([c_void_p, c_int32, c_int32], c_int32),
     "qsw_op_schedule": ([c_void_p, POINTER(c_int32), POINTER(c_int32)], c_int32),
     "qsw_server_create": ([c_int32, POINTER(qsw_server_config), POINTER(c_void_p)], c_int32),
     "qsw_server_submit": ([c_void_p, POINTER(qsw_request), POINTER(c_int64)], c_int32),
@@ -505,6 +506,11 @@ def qsw_tune_reset() -> None:
 def qsw_batch_set_schedule(ctx, cluster_size: int = 0, small_limit: int = -1) -> None:
     """Fix the batched series phase's schedule for this context (0 / -1: tuned)."""
     _check(lib().qsw_batch_set_schedule(ctx, int(cluster_size), int(small_limit)), ctx)
+
+
+def qsw_op_set_csr_schedule(op, lanes_per_row: int, unroll: int = 2, ctx=None) -> None:
+    """Fix a CSR operator's schedule (-1: the sliced form)."""
+    _check(lib().qsw_op_set_csr_schedule(op, int(lanes_per_row), int(unroll)), ctx)
 
 
 def qsw_op_schedule(op, with_unroll: bool = False):
