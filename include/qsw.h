@@ -313,15 +313,17 @@ qsw_status qsw_populations(const qsw_op* op, const double* d_rho_series, int32_t
 /* Statistics of one qsw_batch_series call. */
 typedef struct {
   int32_t walks;        /* walks in the batch */
-  int32_t clusters;     /* thread-block clusters (8 CTAs each) resident in the
-                           series phase (0: every walk was small) */
+  int32_t clusters;     /* thread-block clusters (cluster_size CTAs each)
+                           launched for the series phase (0: every walk was
+                           small) */
   double norms_ms;      /* device time of the 1-norm phase */
   double series_ms;     /* device time of the series phase */
   int64_t matvecs;      /* applications of the walks' L~ to an n x n0 block */
   int64_t fupdates;     /* sum over terms of the outputs updated */
   int32_t small_walks;  /* walks whose two n x n0 Taylor-term blocks fit in
-                           64 KB: run by one thread block each with the terms
-                           in shared memory, alongside the clusters */
+                           small_limit bytes: run by one thread block each
+                           with the terms in shared memory, alongside the
+                           clusters */
   double algorithmic_flops;  /* series phase, all walks: the operator's flops
                                 on every right-hand side (FP32 for complex64
                                 bulk walks, FP64 otherwise) plus the FP64 output

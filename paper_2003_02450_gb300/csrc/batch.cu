@@ -1,13 +1,14 @@
 // Batched L-QSW series: many independent walks of uneven size in one launch.
 //
-// Each walk is handled by one thread-block cluster of kCl CTAs; clusters take
+// Each walk is handled by one thread-block cluster (kCl CTAs in phase 1; in
+// phase 2 the cluster size of the tuned schedule, 4, 8 or 16); clusters take
 // walks from a queue ordered by decreasing size (largest first), so big and
 // small walks pack onto the GPU together.  Inside a cluster every pass over the
 // walk's elements is split over the cluster's warps, and passes are separated
 // by hardware cluster barriers (barrier.cluster: no spin loop).  Reductions go
 // through distributed shared memory: each CTA reduces its part, then every CTA
-// reads the kCl partials in rank order, so all CTAs hold the same value and
-// take the same decisions.
+// reads the cluster's partials in rank order, so all CTAs hold the same value
+// and take the same decisions.
 //
 // Phase 1 (norms): the exact ||L||_1 and, only when Code Fragment 3.1 needs
 // them for the walk's time span (condition (3.13) fails), the Higham--Tisseur
@@ -18,8 +19,8 @@
 // ||B||_inf is the largest row sum of moduli), populations of every output.
 // Hermitian right-hand sides are computed on upper triangles as in series.cu.
 //
-// Small walks (their two Taylor-term blocks fit in 64 KB) take phase 2 on ONE
-// CTA instead, with the Taylor terms in shared memory: for such walks each term
+// Small walks (their two Taylor-term blocks fit in the schedule's one-CTA
+// limit, at most 64 KB) take phase 2 on ONE CTA instead, with the Taylor terms in shared memory: for such walks each term
 // is a few hundred nanoseconds of work, and a cluster's barriers and its
 // gathers of terms written by other SMs (L2 round trips) would dominate.  The
 // small-walk kernel runs on a second stream alongside the cluster kernel.
