@@ -454,15 +454,19 @@ def run_ours(args):
             e2e_step()
         barrier()
         t0 = time.perf_counter()
+        marks = []
         for _ in range(args.steps):
-            e2e_step()
+            e2e_step()   # returns with the step's results on the host
+            marks.append(time.perf_counter())
         torch.cuda.synchronize(dev)
         e_ms = max_over_ranks((time.perf_counter() - t0) * 1000.0 / args.steps, dev)
+        step_ms = [(y - x) * 1000.0 for x, y in zip([t0] + marks[:-1], marks)]
         g = cfg.graph
         h2d = g.rowptr.nbytes + g.col.nbytes + g.w.nbytes + h_rho0.numel() * 16
         d2h = h_out.numel() * 16 + h_pops.numel() * 8
         e2e = {"value": job_value(world, q, e_ms), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "ms_per_step": e_ms,
+               "step_ms": [round(v, 2) for v in step_ms],
                "api": "qsw_build_superoperator + qsw_expmv_series_host (host buffers)"}
 
     cpu = None
