@@ -1333,7 +1333,10 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
   QSW_CUDA_TRY(cudaMemcpyAsync(&h, op.ctrl.p, offsetof(Ctrl, gmax), cudaMemcpyDeviceToHost, st));
   if (a.progress) {
     // hand finished outputs to the sink while the kernel runs; the loop ends
-    // when the kernel has (its grid barriers bound every wait inside it)
+    // when the kernel has (its grid barriers bound every wait inside it).  The
+    // thread yields between polls instead of sleeping: on a loaded host a
+    // timed sleep overslept by up to ~15 ms now and then, which delayed the
+    // last copies by as much.
     int seen = 0;
     for (;;) {
       const bool done = cudaEventQuery(ev1) != cudaErrorNotReady;
@@ -1343,7 +1346,7 @@ void run_series(Op& op, const double* d_rho0, double t0, double dt, int steps, d
         seen = k;
       }
       if (done) break;
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::yield();
     }
   }
   QSW_CUDA_TRY(cudaStreamSynchronize(st));
