@@ -1313,7 +1313,9 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
   QSW_CUDA_TRY(cudaEventRecord(e2, st));
   if (sink) {
     // hand finished walks out while the kernels run; the loop ends when both
-    // kernels have (their waits are cluster barriers, which always complete)
+    // kernels have (their waits are cluster barriers, which always complete).
+    // The thread yields between polls: a timed sleep can overshoot by
+    // milliseconds on a loaded host, and each overshoot delays a walk's result.
     std::vector<char> seen(count, 0);
     for (;;) {
       const bool done = cudaEventQuery(e2) != cudaErrorNotReady;
@@ -1323,7 +1325,7 @@ void run_batch(qsw_ctx* ctx, int count, Op* const* ops, const double* const* d_r
           sink->ready(w);
         }
       if (done) break;
-      std::this_thread::sleep_for(std::chrono::microseconds(20));
+      std::this_thread::yield();
     }
   }
   std::vector<long long> hc(4 * count);
