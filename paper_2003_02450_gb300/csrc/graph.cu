@@ -273,7 +273,7 @@ __global__ void prep_mf_kernel(int N, int Nt, double omw, const int* __restrict_
 // term; uniform-degree windows keep the natural order).  One block of 64
 // threads per window.
 __global__ void window_rows_kernel(int N, int Nt, const int* __restrict__ hrow, int* prow,
-                                   int* pwin) {
+                                   int* pwin, int* pmax) {
   __shared__ int len[64];
   __shared__ int by_rank[64];
   __shared__ int cost_nat[2], cost_pair;
@@ -297,7 +297,37 @@ __global__ void window_rows_kernel(int N, int Nt, const int* __restrict__ hrow, 
   const bool paired = 100 * cost_pair <= 85 * (cost_nat[0] + cost_nat[1]);
   const int slot = paired ? (rank < 32 ? rank : 32 + (63 - rank)) : k;
   prow[w0 + slot] = i < Nt ? i : -1;
-  if (k == 0) pwin[blockIdx.x] = paired ? 1 : 0;
+  if (k == 0) {
+    pwin[blockIdx.x] = paired ? 1 : 0;
+    pmax[blockIdx.x] = paired ? cost_pair : 0;   // longest merged list of the window
+  }
+}
+
+// Paired windows' merged part-A lists, lane-interleaved: entry t of lane l
+// (row a = prow[w0 + l]'s entries, then row b = prow[w0 + 32 + l]'s) at
+// 32 (paoff[w] + t) + l; entries past a lane's list are zero (never read).
+__global__ void pair_lists_kernel(int N, const int* __restrict__ hrow, const int* __restrict__ hcol,
+                                  const double* __restrict__ hval64,
+                                  const float* __restrict__ hval32, const int* __restrict__ prow,
+                                  const int* __restrict__ pwin, const int* __restrict__ paoff,
+                                  int* __restrict__ pacol, double* __restrict__ paval64,
+                                  float* __restrict__ paval32) {
+  const int w = blockIdx.x, l = threadIdx.x;
+  if (!pwin[w]) return;
+  const int a = prow[64 * w + l], b = prow[64 * w + 32 + l];
+  const int ea = (a >= 0 && a < N) ? hrow[a] : 0;
+  const int la = (a >= 0 && a < N) ? hrow[a + 1] - ea : 0;
+  const int eb = (b >= 0 && b < N) ? hrow[b] : 0;
+  const int lb = (b >= 0 && b < N) ? hrow[b + 1] - eb : 0;
+  const int m = paoff[w + 1] - paoff[w];
+  for (int t = 0; t < m; ++t) {
+    const long long d = 32LL * (paoff[w] + t) + l;
+    const int e = t < la ? ea + t : eb + (t - la);
+    const bool live = t < la + lb;
+    pacol[d] = live ? hcol[e] : 0;
+    paval64[d] = live ? hval64[e] : 0.0;
+    paval32[d] = live ? hval32[e] : 0.0f;
+  }
 }
 
 template <class T>
@@ -318,7 +348,8 @@ void scan_counts(DevBuf& cnt, DevBuf& rowptr, int n, cudaStream_t st) {
 
 // Off-diagonal entries of G^u = max(G, G^T) (union_count_kernel's total):
 // rows of G and of its transpose merged, counting distinct columns.  O(nnz).
-int undirected_offdiag(int N, const std::vector<int>& rowptr, const std::vector<int>& col) {
+int undirected_offdiag(int N, const std::vector<int>& rowptr, const std::vector<int>& col,
+                       std::vector<int>& rowlen) {
   std::vector<int> tr(N + 1, 0), tc(col.size());
   for (int c : col) ++tr[c + 1];
   for (int i = 0; i < N; ++i) tr[i + 1] += tr[i];
@@ -326,6 +357,7 @@ int undirected_offdiag(int N, const std::vector<int>& rowptr, const std::vector<
   for (int i = 0; i < N; ++i)
     for (int e = rowptr[i]; e < rowptr[i + 1]; ++e) tc[fill[col[e]]++] = i;   // rows in order
   long long total = 0;
+  rowlen.assign(N, 0);
   for (int i = 0; i < N; ++i) {
     int a = rowptr[i], b = tr[i];
     while (a < rowptr[i + 1] || b < tr[i + 1]) {
@@ -334,6 +366,7 @@ int undirected_offdiag(int N, const std::vector<int>& rowptr, const std::vector<
       if (ca <= cb) ++a;
       if (cb <= ca) ++b;
       ++total;
+      ++rowlen[i];
     }
   }
   return (int)total;
@@ -384,7 +417,7 @@ void build_graph(Op& op) {
         N, g.g_rowptr.as<int>(), g.g_col.as<int>(), g.gt_rowptr.as<int>(), g.gt_col.as<int>(),
         g.scratch.as<int>());
     scan_counts(g.scratch, g.hoff_rowptr, N, st);
-    g.nnz_hoff = undirected_offdiag(N, op.g_rowptr, op.g_col);
+    g.nnz_hoff = undirected_offdiag(N, op.g_rowptr, op.g_col, g.hlen);
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
     QSW_LAUNCH laplacian_fill_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
@@ -400,8 +433,13 @@ void build_graph(Op& op) {
                                                                g.scratch.as<int>());
     scan_counts(g.scratch, g.hoff_rowptr, N, st);
     g.nnz_hoff = 0;   // h_offcount_kernel's total: entries off the diagonal
+    g.hlen.assign(N, 0);
     for (int i = 0; i < N; ++i)
-      for (int e = op.h_rowptr[i]; e < op.h_rowptr[i + 1]; ++e) g.nnz_hoff += op.h_col[e] != i;
+      for (int e = op.h_rowptr[i]; e < op.h_rowptr[i + 1]; ++e)
+        if (op.h_col[e] != i) {
+          ++g.nnz_hoff;
+          ++g.hlen[i];
+        }
     g.hoff_col.alloc(sizeof(int) * (g.nnz_hoff + 1));
     g.hoff_val.alloc(sizeof(double) * (g.nnz_hoff + 1));
     QSW_LAUNCH h_split_kernel<<<grid_for(N, 128, 4096), 128, 0, st>>>(
@@ -472,9 +510,42 @@ void prep_matfree(Op& op) {
   const int nwin = (Nt + 63) / 64;
   m.prow.alloc(sizeof(int) * 64 * (size_t)nwin);
   m.pwin.alloc(sizeof(int) * (size_t)nwin);
-  QSW_LAUNCH window_rows_kernel<<<nwin, 64, 0, st>>>(op.omega < 1.0 ? g.N : 0, Nt,
-                                                     g.hoff_rowptr.as<int>(), m.prow.as<int>(),
-                                                     m.pwin.as<int>());
+  DevBuf pmax;
+  pmax.alloc(sizeof(int) * (size_t)nwin);
+  const int nh_rows = op.omega < 1.0 ? g.N : 0;
+  QSW_LAUNCH window_rows_kernel<<<nwin, 64, 0, st>>>(nh_rows, Nt, g.hoff_rowptr.as<int>(),
+                                                     m.prow.as<int>(), m.pwin.as<int>(),
+                                                     pmax.as<int>());
+  QSW_CUDA_TRY(cudaGetLastError());
+  // the paired windows' interleaved lists: offsets by a scan on the device;
+  // the storage is sized on the host, without a read-back, by a bound: a
+  // window's longest merged list is at most its two longest rows together
+  m.paoff.alloc(sizeof(int) * ((size_t)nwin + 1));
+  QSW_LAUNCH scan_small_kernel<<<1, 1024, 0, st>>>(pmax.as<int>(), m.paoff.as<int>(), nwin);
+  QSW_CUDA_TRY(cudaGetLastError());
+  long long bound = 0;
+  QSW_CHECK_ARG((int)g.hlen.size() >= nh_rows, QSW_ERR_CUDA, "H row lengths missing on the host");
+  for (int w = 0; w < nwin && nh_rows > 0; ++w) {
+    int top1 = 0, top2 = 0;
+    for (int i = 64 * w; i < std::min(64 * w + 64, nh_rows); ++i) {
+      const int l = g.hlen[i];
+      if (l > top1) {
+        top2 = top1;
+        top1 = l;
+      } else if (l > top2) {
+        top2 = l;
+      }
+    }
+    bound += top1 + top2;
+  }
+  const size_t pe = 32 * (size_t)std::max(1LL, bound);
+  m.pacol.alloc(sizeof(int) * pe);
+  m.paval64.alloc(sizeof(double) * pe);
+  m.paval32.alloc(sizeof(float) * pe);
+  QSW_LAUNCH pair_lists_kernel<<<nwin, 32, 0, st>>>(
+      nh_rows, g.hoff_rowptr.as<int>(), g.hoff_col.as<int>(), m.hval64.as<double>(),
+      m.hval32.as<float>(), m.prow.as<int>(), m.pwin.as<int>(), m.paoff.as<int>(),
+      m.pacol.as<int>(), m.paval64.as<double>(), m.paval32.as<float>());
   QSW_CUDA_TRY(cudaGetLastError());
   // entries of the CSR form: diagonal + commutator stripes/blocks + one per jump
   const long long n = (long long)Nt * Nt;

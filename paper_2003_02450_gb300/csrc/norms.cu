@@ -479,7 +479,7 @@ mf_box_kernel(MfOp<double> op, const int* __restrict__ list, const int* __restri
       double ox[2], oy[2];
       if (all_rows) {
         mf_window_rows(op.prow, i0, lane, op.Nt - 1, irow);
-        mf_window_apply<double, double2, ADJ>(op, x, j, i0, irow, ox, oy);
+        mf_window_apply<double, double2, ADJ, LdGlobal, true>(op, x, j, i0, irow, ox, oy);
       } else {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
@@ -531,7 +531,7 @@ mf_herm_kernel(MfOp<R> op, int cols, long long n, R scale, const VT* __restrict_
       const VT* xc = x + c * n;
       VT* yc = y + c * n;
       R ox[2], oy[2];
-      mf_window_apply<R, VT, ADJ>(op, xc, j, i0, irow, ox, oy);
+      mf_window_apply<R, VT, ADJ, LdGlobal, true>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
       for (int u = 0; u < 2; ++u) {
         const int i = irow[u];

@@ -32,6 +32,7 @@ struct GraphDev {
   DevBuf hdiag;                      // [Nt] diagonal of H (0 beyond N)
   DevBuf hoff_rowptr, hoff_col, hoff_val;  // off-diagonal H, N rows
   int nnz_hoff = 0;
+  std::vector<int> hlen;             // host: entries of each off-diagonal H row
   DevBuf src_v, src_r, snk_v, snk_r;       // ports
   int n_src = 0, n_snk = 0;
   // jump lists (coefficient included, omega-scaled for graph arcs)
@@ -72,6 +73,8 @@ struct MfData {
   DevBuf habs;             // [Nt] sum_m |(1 - omega) H_vm|, for the exact 1-norm
   DevBuf prow;             // [64 ceil(Nt / 64)] lane order of each 64-row window
   DevBuf pwin;             // [ceil(Nt / 64)] 1 where that order pairs the rows
+  DevBuf paoff;            // [ceil(Nt / 64) + 1] paired windows' list offsets (in rows of 32)
+  DevBuf pacol, paval64, paval32;   // their lane-interleaved merged part-A lists
 };
 
 // A complex matrix in CSR on the host (columns increasing within a row).

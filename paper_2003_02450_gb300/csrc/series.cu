@@ -710,7 +710,7 @@ mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__
       for (int c = 0; c < cols; ++c) {
         const VT* xc = x + c * n;
         R ox[kRpt], oy[kRpt];
-        mf_window_apply<R, VT, ADJ>(op, xc, j, i0, irow, ox, oy);
+        mf_window_apply<R, VT, ADJ, LdGlobal, true>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
         for (int u = 0; u < kRpt; ++u) {
           if (irow[u] < 0) continue;
@@ -1154,6 +1154,9 @@ template <class R> MfOp<R> make_mf(const Op& op, bool adjoint) {
                                          : (f ? m.jval32.p : op.g.j_val.p));
   o.prow = m.prow.as<int>();
   o.pwin = m.pwin.as<int>();
+  o.paoff = m.paoff.as<int>();
+  o.pacol = m.pacol.as<int>();
+  o.paval = static_cast<const R*>(f ? m.paval32.p : m.paval64.p);
   return o;
 }
 template MfOp<double> make_mf<double>(const Op&, bool);
