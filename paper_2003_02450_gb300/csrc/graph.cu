@@ -510,18 +510,30 @@ void prep_matfree(Op& op) {
   const int nwin = (Nt + 63) / 64;
   m.prow.alloc(sizeof(int) * 64 * (size_t)nwin);
   m.pwin.alloc(sizeof(int) * (size_t)nwin);
-  DevBuf pmax;
-  pmax.alloc(sizeof(int) * (size_t)nwin);
+  m.pmax.alloc(sizeof(int) * (size_t)nwin);
   const int nh_rows = op.omega < 1.0 ? g.N : 0;
   QSW_LAUNCH window_rows_kernel<<<nwin, 64, 0, st>>>(nh_rows, Nt, g.hoff_rowptr.as<int>(),
                                                      m.prow.as<int>(), m.pwin.as<int>(),
-                                                     pmax.as<int>());
+                                                     m.pmax.as<int>());
   QSW_CUDA_TRY(cudaGetLastError());
-  // the paired windows' interleaved lists: offsets by a scan on the device;
-  // the storage is sized on the host, without a read-back, by a bound: a
-  // window's longest merged list is at most its two longest rows together
+  m.pa_ready = false;   // the interleaved lists follow these values: built on first use
+  // entries of the CSR form: diagonal + commutator stripes/blocks + one per jump
+  const long long n = (long long)Nt * Nt;
+  op.nnz_csr = n + (op.omega < 1.0 ? 2LL * Nt * g.nnz_hoff : 0LL) + g.n_jumps;
+}
+
+void ensure_pair_lists(Op& op) {
+  MfData& m = op.mf;
+  if (m.pa_ready) return;
+  cudaStream_t st = op.ctx->stream;
+  const GraphDev& g = op.g;
+  const int nwin = (g.Nt + 63) / 64;
+  const int nh_rows = op.omega < 1.0 ? g.N : 0;
+  // offsets by a scan on the device; the storage is sized on the host,
+  // without a read-back, by a bound: a window's longest merged list is at
+  // most its two longest rows together
   m.paoff.alloc(sizeof(int) * ((size_t)nwin + 1));
-  QSW_LAUNCH scan_small_kernel<<<1, 1024, 0, st>>>(pmax.as<int>(), m.paoff.as<int>(), nwin);
+  QSW_LAUNCH scan_small_kernel<<<1, 1024, 0, st>>>(m.pmax.as<int>(), m.paoff.as<int>(), nwin);
   QSW_CUDA_TRY(cudaGetLastError());
   long long bound = 0;
   QSW_CHECK_ARG((int)g.hlen.size() >= nh_rows, QSW_ERR_CUDA, "H row lengths missing on the host");
@@ -547,9 +559,7 @@ void prep_matfree(Op& op) {
       m.hval32.as<float>(), m.prow.as<int>(), m.pwin.as<int>(), m.paoff.as<int>(),
       m.pacol.as<int>(), m.paval64.as<double>(), m.paval32.as<float>());
   QSW_CUDA_TRY(cudaGetLastError());
-  // entries of the CSR form: diagonal + commutator stripes/blocks + one per jump
-  const long long n = (long long)Nt * Nt;
-  op.nnz_csr = n + (op.omega < 1.0 ? 2LL * Nt * g.nnz_hoff : 0LL) + g.n_jumps;
+  m.pa_ready = true;
 }
 
 }  // namespace qsw

@@ -1049,6 +1049,7 @@ struct Estimator {
 
 void compute_norms(Op& op, const Csr* L, const Csr* LH) {
   cudaStream_t st = op.ctx->stream;
+  if (!L && !op.gq.active) ensure_pair_lists(op);   // the products below read part A through them
   const int n = (int)op.n;
   // exact ||L||_1 (global walks: closed form when it applies, else estimated below)
   bool one_estimated = false;

@@ -73,8 +73,10 @@ struct MfData {
   DevBuf habs;             // [Nt] sum_m |(1 - omega) H_vm|, for the exact 1-norm
   DevBuf prow;             // [64 ceil(Nt / 64)] lane order of each 64-row window
   DevBuf pwin;             // [ceil(Nt / 64)] 1 where that order pairs the rows
+  DevBuf pmax;             // [ceil(Nt / 64)] longest merged part-A list of each paired window
   DevBuf paoff;            // [ceil(Nt / 64) + 1] paired windows' list offsets (in rows of 32)
   DevBuf pacol, paval64, paval32;   // their lane-interleaved merged part-A lists
+  bool pa_ready = false;   // built (ensure_pair_lists) for the current values
 };
 
 // A complex matrix in CSR on the host (columns increasing within a row).
@@ -151,6 +153,7 @@ void build_jumps(Op& op);           // J, J^T, dtot for op.omega
 void assemble(Op& op, bool adjoint, Csr& out);   // L (adjoint = false) or L^H, FP64 values
 void to_fp32(Op& op, Csr& m);                    // replace FP64 values by FP32
 void prep_matfree(Op& op);         // MfData for op.omega
+void ensure_pair_lists(Op& op);    // the interleaved part-A lists the estimator's products read
 // gqsw.cu
 void build_global(Op& op);                        // device form for op.omega
 template <class R> struct GqOp;

@@ -697,8 +697,9 @@ __global__ void plan_kernel(const double* __restrict__ dp, int prec, double t0, 
 
 // y = scale L x (or scale L^H x) for `cols` vectors stored one after another
 // (n apart), matrix-free.  Blocks stride over the columns j of the density
-// matrix.
-template <class R, class VT, bool ADJ>
+// matrix.  PA: part A through the lane-interleaved lists (built for the
+// operator's current values: MfData::pa_ready).
+template <class R, class VT, bool ADJ, bool PA = false>
 __global__ void __launch_bounds__(kBlock)
 mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__ y, double scale) {
   const long long n = (long long)op.Nt * op.Nt;
@@ -710,7 +711,7 @@ mf_apply_kernel(MfOp<R> op, int cols, const VT* __restrict__ x, VT* __restrict__
       for (int c = 0; c < cols; ++c) {
         const VT* xc = x + c * n;
         R ox[kRpt], oy[kRpt];
-        mf_window_apply<R, VT, ADJ, LdGlobal, true>(op, xc, j, i0, irow, ox, oy);
+        mf_window_apply<R, VT, ADJ, LdGlobal, PA>(op, xc, j, i0, irow, ox, oy);
 #pragma unroll
         for (int u = 0; u < kRpt; ++u) {
           if (irow[u] < 0) continue;
@@ -1165,26 +1166,37 @@ template MfOp<float> make_mf<float>(const Op&, bool);
 void mf_apply64(const Op& op, bool adjoint, int cols, const double* x, double* y, double scale) {
   const MfOp<double> m = make_mf<double>(op, adjoint);
   const unsigned grid = (unsigned)std::min(op.Nt, 152 * 8);
-  if (adjoint)
-    QSW_LAUNCH mf_apply_kernel<double, double2, true><<<grid, kBlock, 0, op.ctx->stream>>>(
-        m, cols, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), scale);
-  else
-    QSW_LAUNCH mf_apply_kernel<double, double2, false><<<grid, kBlock, 0, op.ctx->stream>>>(
-        m, cols, reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(y), scale);
+  const double2* xv = reinterpret_cast<const double2*>(x);
+  double2* yv = reinterpret_cast<double2*>(y);
+  cudaStream_t st = op.ctx->stream;
+  if (op.mf.pa_ready) {
+    if (adjoint)
+      QSW_LAUNCH mf_apply_kernel<double, double2, true, true><<<grid, kBlock, 0, st>>>(m, cols, xv, yv, scale);
+    else
+      QSW_LAUNCH mf_apply_kernel<double, double2, false, true><<<grid, kBlock, 0, st>>>(m, cols, xv, yv, scale);
+  } else {
+    if (adjoint)
+      QSW_LAUNCH mf_apply_kernel<double, double2, true><<<grid, kBlock, 0, st>>>(m, cols, xv, yv, scale);
+    else
+      QSW_LAUNCH mf_apply_kernel<double, double2, false><<<grid, kBlock, 0, st>>>(m, cols, xv, yv, scale);
+  }
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
 // The same in complex64 with the FP32 coefficients (the 1-norm estimator's
 // ranking products).
 void mf_apply32(const Op& op, bool adjoint, int cols, const float* x, float* y, double scale) {
+  QSW_CHECK_ARG(op.mf.pa_ready, QSW_ERR_CUDA, "estimator products before the part-A lists");
   const MfOp<float> m = make_mf<float>(op, adjoint);
   const unsigned grid = (unsigned)std::min(op.Nt, 152 * 8);
+  const float2* xv = reinterpret_cast<const float2*>(x);
+  float2* yv = reinterpret_cast<float2*>(y);
   if (adjoint)
-    QSW_LAUNCH mf_apply_kernel<float, float2, true><<<grid, kBlock, 0, op.ctx->stream>>>(
-        m, cols, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), scale);
+    QSW_LAUNCH mf_apply_kernel<float, float2, true, true><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, xv, yv, scale);
   else
-    QSW_LAUNCH mf_apply_kernel<float, float2, false><<<grid, kBlock, 0, op.ctx->stream>>>(
-        m, cols, reinterpret_cast<const float2*>(x), reinterpret_cast<float2*>(y), scale);
+    QSW_LAUNCH mf_apply_kernel<float, float2, false, true><<<grid, kBlock, 0, op.ctx->stream>>>(
+        m, cols, xv, yv, scale);
   QSW_CUDA_TRY(cudaGetLastError());
 }
 
